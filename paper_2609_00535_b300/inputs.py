@@ -1,0 +1,364 @@
+"""Seeded synthetic inputs: meshes, initial densities and run parameters.
+
+This module holds no arithmetic of the time step.  It builds what a user (and
+the tests and the benchmark) hand to the library: GLL node coordinates of
+isoparametric quad/hex elements, global node ids (equal ids = shared node;
+periodicity is expressed through ids), per-face kinds and wall tags, the
+tanh-initialised density of Appendix A (Eq. dens / A.8) and seeded density
+noise.  The GLL reference points come from numpy's Legendre root finder.
+
+Meshes (the paper's own GMSH meshes are not available; these generators stand
+in for them with the paper's geometry as the shape):
+ * ``box``               affine quads/hexes, walls or periodic per axis
+                         (flat-wall droplet of Sec. 3.1, isolated periodic
+                         droplet of Sec. 3.3);
+ * ``cylinder_ogrid``    curved O-grid around a circular cylinder inside the
+                         unit square (Sec. 3.2, 2D);
+ * ``sphere_cap_box``    box whose bottom is a sphere cap (Sec. 3.2, 3D);
+ * ``rotate_elements``   random proper rotations of the element-local axes, so
+                         that neighbouring elements disagree on orientation
+                         (unstructured connectivity).
+
+Layout of the arrays (the library's mesh ABI):
+  node_xyz  [E][(N+1)^d][d] float64, local node k = i + n j (+ n^2 l), i fastest
+  global_id [E][(N+1)^d]    int64
+  face_kind [E][2d]         uint8, face f = 2 b + s (b = reference axis,
+                            s = 0 for xi_b = -1, 1 for xi_b = +1); 1 = wall
+  face_tag  [E][2d]         int32; wall contact-angle tag: < 0 neutral (90 deg),
+                            0 = theta_w, k >= 1 = theta_tag[k-1]
+"""
+from dataclasses import dataclass, field
+import math
+
+import numpy as np
+from numpy.polynomial import legendre as _leg
+
+
+def gll_points(N):
+    """GLL points of order N (numpy Legendre roots of P_N' plus the end points)."""
+    if N < 1:
+        raise ValueError("N must be >= 1")
+    inner = _leg.Legendre.basis(N).deriv().roots() if N >= 2 else np.zeros(0)
+    return np.concatenate([[-1.0], np.sort(inner.real), [1.0]])
+
+
+@dataclass
+class MeshArrays:
+    dim: int
+    N: int
+    node_xyz: np.ndarray
+    global_id: np.ndarray
+    face_kind: np.ndarray
+    face_tag: np.ndarray
+    name: str = "mesh"
+
+    @property
+    def n_elem(self):
+        return self.node_xyz.shape[0]
+
+    @property
+    def n_local(self):
+        return self.node_xyz.shape[0] * self.node_xyz.shape[1]
+
+    def validate(self):
+        n = self.N + 1
+        E = self.n_elem
+        assert self.node_xyz.shape == (E, n ** self.dim, self.dim)
+        assert self.global_id.shape == (E, n ** self.dim)
+        assert self.face_kind.shape == (E, 2 * self.dim)
+        assert self.face_tag.shape == (E, 2 * self.dim)
+        return self
+
+
+def _local_multi_index(dim, n):
+    """[n^d, d] multi-indices (i, j, l) of the local nodes, i fastest."""
+    idx = np.indices((n,) * dim).reshape(dim, -1)[::-1].T   # columns (i, j, l)
+    return idx
+
+
+def _element_multi_index(ne):
+    dim = len(ne)
+    return np.indices(tuple(ne[::-1])).reshape(dim, -1)[::-1].T  # axis 0 fastest
+
+
+def _structured(ne, N, mapping, periodic, face_tags, name):
+    """Build a mesh on a structured block of elements through a mapping.
+
+    mapping(s) maps block coordinates s in [0,1]^d (array [..., d]) to physical
+    points.  periodic[a] glues the two ends of block axis a.
+    """
+    dim = len(ne)
+    n = N + 1
+    xi = gll_points(N)
+    loc = _local_multi_index(dim, n)                 # [n^d, d]
+    eid = _element_multi_index(ne)                   # [E, d]
+    E = eid.shape[0]
+    ne_arr = np.asarray(ne)
+    s = (eid[:, None, :] + (xi[loc][None, :, :] + 1) / 2) / ne_arr   # [E, n^d, d]
+    node_xyz = mapping(s)
+    I = eid[:, None, :] * N + loc[None, :, :]        # structured node index
+    counts = []
+    for a in range(dim):
+        if periodic[a]:
+            I[..., a] %= ne[a] * N
+            counts.append(ne[a] * N)
+        else:
+            counts.append(ne[a] * N + 1)
+    stride = np.cumprod([1] + counts[:-1])
+    gid = (I * stride).sum(-1).astype(np.int64)
+    kind = np.zeros((E, 2 * dim), dtype=np.uint8)
+    tag = np.zeros((E, 2 * dim), dtype=np.int32)
+    for a in range(dim):
+        for side in (0, 1):
+            on = eid[:, a] == (0 if side == 0 else ne[a] - 1)
+            if periodic[a]:
+                continue
+            kind[on, 2 * a + side] = 1
+            tag[on, 2 * a + side] = face_tags.get(2 * a + side, -1)
+    return MeshArrays(dim, N, np.ascontiguousarray(node_xyz), gid, kind, tag, name).validate()
+
+
+def box(ne, lo, hi, N, periodic=None, face_tags=None, name="box"):
+    """Affine box of prod(ne) elements; face_tags maps domain face 2a+s -> tag."""
+    dim = len(ne)
+    periodic = tuple(periodic) if periodic is not None else (False,) * dim
+    lo = np.asarray(lo, dtype=np.float64)
+    hi = np.asarray(hi, dtype=np.float64)
+    return _structured(ne, N, lambda s: lo + s * (hi - lo), periodic, face_tags or {}, name)
+
+
+def cylinder_ogrid(N, n_theta=64, n_r=16, Rc=0.1, center=(0.5, 0.5), half=0.5, ratio=None,
+                   name="cylinder"):
+    """Curved O-grid between a circle of radius Rc and the square of half-width half.
+
+    Reference axis 0 runs radially outward, axis 1 counter-clockwise around; the
+    radial spacing is geometric with the first layer close to the arc length of
+    one element on the circle.  Inner face (axis 0, s = 0) is the cylinder wall
+    (tag 0), outer face the square's wall (tag -1, neutral).
+    """
+    c = np.asarray(center, dtype=np.float64)
+    if ratio is None:
+        arc = 2 * math.pi * Rc / n_theta
+        gap = half - Rc
+        lo_r, hi_r = 1.0 + 1e-9, 2.0
+        for _ in range(200):   # first layer gap * (r-1)/(r^n - 1) = arc
+            mid = 0.5 * (lo_r + hi_r)
+            first = gap * (mid - 1) / (mid ** n_r - 1)
+            lo_r, hi_r = (mid, hi_r) if first > arc else (lo_r, mid)
+        ratio = 0.5 * (lo_r + hi_r)
+
+    def grade(sr):
+        if abs(ratio - 1.0) < 1e-12:
+            return sr
+        return (ratio ** (n_r * sr) - 1) / (ratio ** n_r - 1)
+
+    def mapping(s):
+        sr, st = s[..., 0], s[..., 1]
+        ph = 2 * math.pi * st
+        cs, sn = np.cos(ph), np.sin(ph)
+        pc = c + Rc * np.stack([cs, sn], -1)
+        scale = half / np.maximum(np.abs(cs), np.abs(sn))
+        ps = c + scale[..., None] * np.stack([cs, sn], -1)
+        return pc + grade(sr)[..., None] * (ps - pc)
+
+    return _structured((n_r, n_theta), N, mapping, (False, True), {0: 0, 1: -1}, name)
+
+
+def sphere_cap_box(N, ne=(16, 16, 16), L=0.5, W=0.5, H=0.25, Rs=0.7, center=(0.25, 0.25, -0.7),
+                   name="sphere"):
+    """Box [0,L]x[0,W] whose bottom is the sphere |x - center| = Rs and top z = H.
+
+    The bottom face (axis 2, s = 0) is the wetting wall (tag 0); the other five
+    sides are neutral walls (tag -1).  Plan-view coordinates are affine; z blends
+    linearly from the sphere to the lid.
+    """
+    cx, cy, cz = center
+
+    def mapping(s):
+        x = s[..., 0] * L
+        y = s[..., 1] * W
+        zb = cz + np.sqrt(Rs ** 2 - (x - cx) ** 2 - (y - cy) ** 2)
+        z = zb * (1 - s[..., 2]) + H * s[..., 2]
+        return np.stack([x, y, z], -1)
+
+    return _structured(tuple(ne), N, mapping, (False, False, False), {4: 0}, name)
+
+
+def _rotations(dim):
+    """Proper signed permutations of the reference axes: (perm, flips)."""
+    import itertools
+    out = []
+    for perm in itertools.permutations(range(dim)):
+        inv = sum(1 for i in range(dim) for j in range(i + 1, dim) if perm[i] > perm[j])
+        for flips in itertools.product((0, 1), repeat=dim):
+            if (inv + sum(flips)) % 2 == 0:
+                out.append((perm, flips))
+    return out
+
+
+def rotate_elements(mesh, seed):
+    """Re-express each element in a randomly rotated local frame (same geometry)."""
+    dim, N = mesh.dim, mesh.N
+    n = N + 1
+    rng = np.random.default_rng(seed)
+    rots = _rotations(dim)
+    loc = _local_multi_index(dim, n)
+    stride = n ** np.arange(dim)
+    xyz = mesh.node_xyz.copy()
+    gid = mesh.global_id.copy()
+    kind = mesh.face_kind.copy()
+    tag = mesh.face_tag.copy()
+    for e in range(mesh.n_elem):
+        perm, flips = rots[rng.integers(len(rots))]
+        old = np.empty_like(loc)
+        for bn in range(dim):          # new axis bn reads old axis perm[bn]
+            old[:, perm[bn]] = (N - loc[:, bn]) if flips[bn] else loc[:, bn]
+        src = (old * stride).sum(-1)
+        xyz[e] = mesh.node_xyz[e, src]
+        gid[e] = mesh.global_id[e, src]
+        for bn in range(dim):
+            for sn in (0, 1):
+                fo = 2 * perm[bn] + (sn ^ flips[bn])
+                kind[e, 2 * bn + sn] = mesh.face_kind[e, fo]
+                tag[e, 2 * bn + sn] = mesh.face_tag[e, fo]
+    return MeshArrays(dim, N, xyz, gid, kind, tag, mesh.name + "-rot").validate()
+
+
+def min_node_spacing(mesh):
+    """Smallest distance between neighbouring GLL nodes along any reference axis."""
+    n = mesh.N + 1
+    X = mesh.node_xyz.reshape((mesh.n_elem,) + (n,) * mesh.dim + (mesh.dim,))
+    h = np.inf
+    for b in range(mesh.dim):
+        ax = mesh.dim - b
+        dx = np.diff(X, axis=ax)
+        h = min(h, float(np.sqrt((dx ** 2).sum(-1)).min()))
+    return h
+
+
+def tanh_profile(dist, delta, rho_l, rho_v):
+    """Appendix A (Eq. dens): liquid where the signed distance is negative."""
+    return 0.5 * (rho_l + rho_v) - 0.5 * (rho_l - rho_v) * np.tanh(2 * dist / delta)
+
+
+def droplet_density(mesh, x0, R, delta, rho_l=1.0, rho_v=0.1, periodic_L=None):
+    """Eq. A.8: rho = tanh profile of |x - x0| - R at every element-local node."""
+    d = mesh.node_xyz - np.asarray(x0, dtype=np.float64)
+    if periodic_L is not None:   # minimum-image distance in a periodic box
+        Lp = np.asarray(periodic_L, dtype=np.float64)
+        d = d - Lp * np.round(d / Lp)
+    dist = np.sqrt((d ** 2).sum(-1)) - R
+    return tanh_profile(dist, delta, rho_l, rho_v)
+
+
+_M64 = np.uint64(0xFFFFFFFFFFFFFFFF)
+
+
+def splitmix64(x):
+    """SplitMix64 finaliser (Steele, Lea & Flood 2014) on uint64 arrays."""
+    with np.errstate(over="ignore"):
+        z = (np.asarray(x, dtype=np.uint64) + np.uint64(0x9E3779B97F4A7C15)) & _M64
+        z = ((z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)) & _M64
+        z = ((z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)) & _M64
+        return z ^ (z >> np.uint64(31))
+
+
+def node_noise(mesh, seed, amplitude):
+    """Uniform(-a, a) noise per GLL node, keyed by global id (continuous field)."""
+    key = np.uint64(seed) ^ mesh.global_id.astype(np.uint64)
+    u = (splitmix64(key) >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+    return amplitude * (2 * u - 1)
+
+
+# ---------------------------------------------------------------------------
+# The workloads.  Each returns a Case with everything the library's create()
+# takes plus the initial density and the number of steps.
+# ---------------------------------------------------------------------------
+SPEED_MAX = {"D2Q9": math.sqrt(2.0), "D3Q13": math.sqrt(5.0 / 3.0)}   # max |e_alpha|
+
+
+@dataclass
+class Case:
+    name: str
+    mesh: MeshArrays
+    lattice: str
+    rho_l: float
+    rho_v: float
+    beta: float
+    kappa: float
+    tau: float
+    dt: float
+    theta_w: float
+    theta_tag: tuple = ()
+    rho0: np.ndarray = None
+    steps: int = 0
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def nodes(self):
+        return self.mesh.n_local
+
+
+def kappa_from_width(beta, delta, rho_l, rho_v):
+    """Appendix A parameter relation kappa = beta delta^2 (rho_l - rho_v)^2 / 8."""
+    return beta * delta ** 2 * (rho_l - rho_v) ** 2 / 8
+
+
+def cfl_dt(mesh, lattice, cfl=0.5):
+    return cfl * min_node_spacing(mesh) / SPEED_MAX[lattice]
+
+
+def flat_wall_2d(N=4, ne=(8, 8), theta=math.radians(60), R=0.25, beta=1e-3, tau=0.5,
+                 width_spacings=4.0, rho_l=1.0, rho_v=0.1, steps=200, cfl=0.5, seed=None,
+                 noise=0.0):
+    """Sessile half-disc on the wall y = 0 of the unit square (Sec. 3.1 shape)."""
+    mesh = box(ne, (0.0, 0.0), (1.0, 1.0), N, face_tags={2: 0})
+    delta = width_spacings * (1.0 / ne[0]) / N
+    kappa = kappa_from_width(beta, delta, rho_l, rho_v)
+    rho0 = droplet_density(mesh, (0.5, 0.0), R, delta, rho_l, rho_v)
+    if noise:
+        rho0 = rho0 + node_noise(mesh, seed or 0, noise)
+    return Case("flat2d", mesh, "D2Q9", rho_l, rho_v, beta, kappa, tau, cfl_dt(mesh, "D2Q9", cfl),
+                theta, (), rho0, steps, {"delta": delta})
+
+
+def cylinder_2d(theta=math.radians(90), N=6, n_theta=64, n_r=16, Rc=0.1, beta=1e-2, tau=0.5,
+                rho_l=1.0, rho_v=0.1, noise=1e-3, seed=1, perm_seed=2, cfl=0.5, steps=200):
+    """Droplet of radius 0.3 Rc touching a cylinder (Sec. 3.2 shape), curved O-grid."""
+    mesh = rotate_elements(cylinder_ogrid(N, n_theta, n_r, Rc), perm_seed)
+    Rd = 0.3 * Rc
+    spacing = 2 * math.pi * Rc / n_theta / N
+    delta = 4 * spacing
+    kappa = kappa_from_width(beta, delta, rho_l, rho_v)
+    rho0 = droplet_density(mesh, (0.5, 0.5 + Rc + Rd), Rd, delta, rho_l, rho_v)
+    rho0 = rho0 + node_noise(mesh, seed, noise)
+    return Case("cylinder2d", mesh, "D2Q9", rho_l, rho_v, beta, kappa, tau,
+                cfl_dt(mesh, "D2Q9", cfl), theta, (), rho0, steps, {"delta": delta})
+
+
+def sphere_3d(N=5, ne=(16, 16, 16), theta=math.radians(60), beta=1e-3, Cn=0.08, d=0.25,
+              La=60.0, rho_l=1.0, rho_v=0.1, cfl=0.5, steps=20000):
+    """3D droplet (d = 0.25 at (0.25, 0.25, 0.04)) on a sphere-cap bottom (Sec. 3.2)."""
+    mesh = sphere_cap_box(N, ne)
+    delta = Cn * d
+    kappa = kappa_from_width(beta, delta, rho_l, rho_v)
+    dt = cfl_dt(mesh, "D3Q13", cfl)
+    gamma = (rho_l - rho_v) ** 3 * math.sqrt(2 * kappa * beta) / 6
+    eta = math.sqrt(gamma * d / La)          # La = gamma d / eta^2
+    nu = eta / rho_l
+    tau = nu / ((1.0 / 3.0) * dt)            # nu = tau c_s^2 dt
+    rho0 = droplet_density(mesh, (0.25, 0.25, 0.04), d / 2, delta, rho_l, rho_v)
+    return Case("sphere3d", mesh, "D3Q13", rho_l, rho_v, beta, kappa, tau, dt, theta, (),
+                rho0, steps, {"delta": delta, "La": La})
+
+
+def periodic_droplet(dim=2, ne=4, N=8, L=1.0, D=0.5, Cn=0.063, beta=1e-3, tau=0.5,
+                     rho_l=1.0, rho_v=0.1, cfl=0.5, steps=200):
+    """Isolated droplet in a periodic box (Sec. 3.3)."""
+    mesh = box((ne,) * dim, (0.0,) * dim, (L,) * dim, N, periodic=(True,) * dim)
+    delta = Cn * D
+    kappa = kappa_from_width(beta, delta, rho_l, rho_v)
+    lat = "D2Q9" if dim == 2 else "D3Q13"
+    rho0 = droplet_density(mesh, (L / 2,) * dim, D / 2, delta, rho_l, rho_v)
+    return Case("droplet%dd" % dim, mesh, lat, rho_l, rho_v, beta, kappa, tau,
+                cfl_dt(mesh, lat, cfl), math.pi / 2, (), rho0, steps, {"delta": delta})

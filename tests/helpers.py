@@ -1,0 +1,22 @@
+"""Shared test helpers: build the oracle for a Case (test-only)."""
+import numpy as np
+
+from oracle import geometry, lattice, method
+
+
+def oracle_mesh(mesh):
+    return geometry.Mesh(mesh.dim, mesh.N, mesh.node_xyz, mesh.global_id, mesh.face_kind,
+                         mesh.face_tag)
+
+
+def oracle_of(case, **over):
+    om = oracle_mesh(case.mesh)
+    lat = lattice.by_name(case.lattice)
+    kw = dict(rho_l=case.rho_l, rho_v=case.rho_v, beta=case.beta, kappa=case.kappa,
+              tau=case.tau, dt=case.dt, theta_w=case.theta_w, theta_tag=case.theta_tag)
+    kw.update(over)
+    return om, method.SemLbm(om, lat, method.Params(**kw))
+
+
+def local_shape(case):
+    return (case.mesh.n_elem,) + (case.mesh.N + 1,) * case.mesh.dim

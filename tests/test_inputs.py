@@ -1,0 +1,78 @@
+"""Checks of the seeded input generators (meshes, densities, noise)."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2609_00535_b300 import inputs
+
+
+def _check_ids(mesh, periodic_L=None):
+    x = mesh.node_xyz.reshape(-1, mesh.dim)
+    g = mesh.global_id.ravel()
+    order = np.argsort(g, kind="stable")
+    gs, xs = g[order], x[order]
+    same = gs[1:] == gs[:-1]
+    d = xs[1:][same] - xs[:-1][same]
+    if periodic_L is not None:
+        L = np.asarray(periodic_L)
+        d = d - L * np.round(d / L)
+    assert np.abs(d).max(initial=0) < 1e-13
+    # distinct ids are distinct points (no unglued copies)
+    uniq = np.unique(g)
+    first = xs[np.r_[True, ~same]]
+    if periodic_L is None:
+        key = np.round(first / 1e-9).astype(np.int64)
+        assert len(np.unique(key, axis=0)) == len(uniq)
+
+
+@pytest.mark.parametrize("mk", [
+    lambda: inputs.box((3, 2), (0, 0), (1, 1), 4),
+    lambda: inputs.rotate_elements(inputs.box((2, 2, 2), (0, 0, 0), (1, 1, 1), 3), 1),
+    lambda: inputs.cylinder_ogrid(4, n_theta=8, n_r=2),
+    lambda: inputs.rotate_elements(inputs.cylinder_ogrid(5, n_theta=8, n_r=2), 3),
+    lambda: inputs.sphere_cap_box(3, ne=(2, 3, 2)),
+])
+def test_shared_ids_are_shared_points(mk):
+    _check_ids(mk())
+
+
+def test_periodic_ids():
+    m = inputs.box((3, 2), (0, 0), (1.5, 1.0), 4, periodic=(True, True))
+    _check_ids(m, periodic_L=(1.5, 1.0))
+    assert len(np.unique(m.global_id)) == 12 * 8
+    assert m.face_kind.sum() == 0
+
+
+def test_rotation_preserves_geometry_and_walls():
+    m = inputs.box((2, 2), (0, 0), (1, 1), 4, face_tags={2: 0})
+    r = inputs.rotate_elements(m, 5)
+    for e in range(m.n_elem):
+        a = np.sort(m.node_xyz[e].round(12).view("f8,f8").ravel())
+        b = np.sort(r.node_xyz[e].round(12).view("f8,f8").ravel())
+        assert (a == b).all()
+        # same multiset of (kind, tag) over the faces
+        assert sorted(zip(m.face_kind[e], m.face_tag[e])) == sorted(zip(r.face_kind[e], r.face_tag[e]))
+
+
+def test_noise_is_seeded_and_keyed_by_global_id():
+    m = inputs.box((2, 2), (0, 0), (1, 1), 4)
+    a = inputs.node_noise(m, 7, 1e-3)
+    b = inputs.node_noise(m, 7, 1e-3)
+    c = inputs.node_noise(m, 8, 1e-3)
+    assert (a == b).all() and not (a == c).all()
+    assert np.abs(a).max() <= 1e-3
+    g = m.global_id.ravel()
+    av = a.ravel()
+    for gid in np.unique(g)[:50]:
+        assert np.ptp(av[g == gid]) == 0.0
+    # SplitMix64 reference value: state 0 -> 0xE220A8397B1DCDAF (first output, seed 0)
+    assert int(inputs.splitmix64(np.array([0], dtype=np.uint64))[0]) == 0xE220A8397B1DCDAF
+
+
+def test_configs_shapes():
+    c1 = inputs.flat_wall_2d()
+    assert c1.nodes == 1600 and c1.mesh.n_elem == 64
+    c2 = inputs.cylinder_2d()
+    assert c2.mesh.n_elem == 1024 and c2.nodes == 1024 * 49
+    assert abs(c1.kappa - 1e-3 * 0.125 ** 2 * 0.81 / 8) < 1e-18

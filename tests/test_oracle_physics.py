@@ -1,0 +1,145 @@
+"""Physics pins of the oracle: closed-form equilibria and conservation laws.
+
+* Appendix A: the planar tanh profile is an equilibrium (mu = 0), and the
+  radial one carries exactly mu0 - kappa (rho'' + (d-1) rho'/r);
+* Sec. 2.2: a planar interface meeting a wall at theta satisfies the wetting
+  gradient exactly, so its discrete mu is small only under the right normal
+  and angle convention;
+* Sec. 1 / Sec. 2.2: flux bounce-back conserves mass to round-off;
+* uniform states at rho_l, rho_v (any wall angle) are stationary;
+* collision conserves mass and momentum.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2609_00535_b300 import inputs
+from oracle import lattice, method
+from tests.helpers import oracle_mesh, oracle_of, local_shape
+
+
+def _solver(mesh, **kw):
+    lat = lattice.d2q9() if mesh.dim == 2 else lattice.d3q13()
+    om = oracle_mesh(mesh)
+    return om, method.SemLbm(om, lat, method.Params(dt=0.01, **kw))
+
+
+def _slab_residual(N, mu0_factor=2.0):
+    mesh = inputs.box((8, 1), (0, 0), (1.0, 0.25), N, periodic=(True, True))
+    om, s = _solver(mesh, beta=1e-3, delta=0.05, mu0_factor=mu0_factor)
+    x = mesh.node_xyz[..., 0]
+    rho = inputs.tanh_profile(np.abs(x - 0.5) - 0.25, 0.05, 1.0, 0.1).reshape(om.shape)
+    mu = s.chemical_potential(rho)
+    return np.abs(mu).max() / np.abs(s.mu0(rho)).max()
+
+
+def test_planar_tanh_is_equilibrium_spectrally():
+    r = [_slab_residual(N) for N in (6, 10, 16)]
+    assert r[2] < 2e-4, r
+    assert r[1] < 0.3 * r[0] and r[2] < 0.3 * r[1], r
+    # the printed factor of Eq. (chemi) without the 2 leaves an O(1) residual
+    assert _slab_residual(16, mu0_factor=1.0) > 0.3
+
+
+def _radial_error(N, dim=2, ne=4, delta=0.08):
+    mesh = inputs.box((ne,) * dim, (0,) * dim, (1.0,) * dim, N, periodic=(True,) * dim)
+    om, s = _solver(mesh, beta=1e-3, delta=delta)
+    x0 = np.array([0.513, 0.493, 0.507][:dim])     # off-node centre (r > 0 at every node)
+    R, amp = 0.25, 0.45
+    r = np.sqrt(((mesh.node_xyz - x0) ** 2).sum(-1)).reshape(om.shape)
+    rho = 0.55 - amp * np.tanh(2 * (r - R) / delta)
+    sech2 = 1 / np.cosh(2 * (r - R) / delta) ** 2
+    d1 = -amp * (2 / delta) * sech2
+    d2 = amp * (8 / delta ** 2) * np.tanh(2 * (r - R) / delta) * sech2
+    exact = s.mu0(rho) - s.p.kappa * (d2 + (dim - 1) * d1 / r)
+    mu = s.chemical_potential(rho)
+    scale = np.abs(s.p.kappa * (dim - 1) * d1 / r).max()     # the curvature part
+    return np.abs(mu - exact).max() / scale
+
+
+def test_radial_profile_chemical_potential():
+    """A circular tanh interface: the discrete mu converges spectrally to
+    mu0(rho) - kappa (rho'' + rho'/r), i.e. the curvature term is captured."""
+    e = [_radial_error(N) for N in (8, 12, 16)]
+    assert e[2] < 0.01 and e[1] < 0.3 * e[0] and e[2] < 0.3 * e[1], e
+
+
+def _tilted_residual(theta, flip=False, N=16):
+    mesh = inputs.box((8, 2), (0, 0), (1.0, 0.25), N, face_tags={2: 0, 3: 1})
+    th_b, th_t = (theta, math.pi - theta) if not flip else (math.pi - theta, theta)
+    om, s = _solver(mesh, beta=1e-3, delta=0.05, theta_w=th_b, theta_tag=(th_t,))
+    x, y = mesh.node_xyz[..., 0], mesh.node_xyz[..., 1]
+    dist = math.sin(theta) * (x - 0.5) + math.cos(theta) * y     # liquid where dist < 0
+    rho = inputs.tanh_profile(dist, 0.05, 1.0, 0.1).reshape(om.shape)
+    mu = s.chemical_potential(rho)
+    return np.abs(mu).max() / np.abs(s.mu0(rho)).max()
+
+
+@pytest.mark.parametrize("deg", [45, 60, 75, 120])
+def test_wetting_condition_holds_for_inclined_interface(deg):
+    th = math.radians(deg)
+    good = _tilted_residual(th)
+    bad = _tilted_residual(th, flip=True)
+    coarse = _tilted_residual(th, N=8)
+    assert good < 2e-3 and good < 0.1 * coarse, (good, coarse)   # spectral convergence
+    assert bad > 1000 * good, (good, bad)                           # wrong orientation: O(10)
+
+
+def test_uniform_states_are_stationary():
+    mesh = inputs.rotate_elements(inputs.box((3, 3), (0, 0), (1, 1), 4, face_tags={2: 0, 0: 1}), 4)
+    for rho0, th in ((1.0, math.radians(30)), (0.1, math.radians(150)), (0.55, math.pi / 2)):
+        om, s = _solver(mesh, beta=1e-3, delta=0.1, theta_w=th, theta_tag=(math.radians(70),)
+                        if rho0 != 0.55 else (math.pi / 2,))
+        f0 = s.initial_state(np.full(om.shape, rho0))
+        f = s.run(f0, 300)
+        np.testing.assert_allclose(f, f0, rtol=0, atol=1e-15 * rho0)
+
+
+def test_mass_conserved_flat_wall_1000_steps():
+    c = inputs.flat_wall_2d()
+    om, s = oracle_of(c)
+    f = s.initial_state(c.rho0.reshape(om.shape))
+    m0 = s.diagnostics(f)["mass"]
+    f = s.run(f, 1000)
+    d = s.diagnostics(f)
+    assert d["n_nonfinite"] == 0
+    assert abs(d["mass"] - m0) < 1e-12 * m0
+    assert d["ke_max"] < 1e-5
+
+
+def test_mass_conserved_curved_rotated_walls():
+    mesh = inputs.rotate_elements(inputs.cylinder_ogrid(5, n_theta=8, n_r=3), 9)
+    c = inputs.Case("cyl", mesh, "D2Q9", 1.0, 0.1, 1e-2, inputs.kappa_from_width(1e-2, 0.05, 1, .1),
+                    0.5, inputs.cfl_dt(mesh, "D2Q9"), math.radians(40))
+    om, s = oracle_of(c)
+    rho = inputs.droplet_density(mesh, (0.5, 0.63), 0.05, 0.05) + inputs.node_noise(mesh, 1, 1e-3)
+    f = s.initial_state(rho.reshape(om.shape))
+    m0 = s.diagnostics(f)["mass"]
+    f = s.run(f, 200)
+    assert abs(s.diagnostics(f)["mass"] - m0) < 1e-13 * m0
+
+
+def test_mass_conserved_3d_sphere():
+    c = inputs.sphere_3d(N=3, ne=(2, 2, 2), Cn=0.3)
+    om, s = oracle_of(c)
+    f = s.initial_state(c.rho0.reshape(om.shape))
+    m0 = s.diagnostics(f)["mass"]
+    f = s.run(f, 100)
+    d = s.diagnostics(f)
+    assert d["n_nonfinite"] == 0 and abs(d["mass"] - m0) < 1e-13 * m0
+
+
+def test_collision_conserves_mass_and_momentum():
+    c = inputs.flat_wall_2d(N=5, ne=(3, 3), noise=1e-2, seed=3)
+    om, s = oracle_of(c)
+    rng = np.random.default_rng(0)
+    f = s.initial_state(c.rho0.reshape(om.shape))
+    f = f * (1 + 1e-2 * rng.standard_normal(f.shape))
+    f = 0.5 * (f + f[:, :, :, :])   # any state with equal shared copies is fine here
+    rho = s.density(f)
+    mu = s.chemical_potential(rho)
+    fs = s.collide(f, rho, mu)
+    np.testing.assert_allclose(fs.sum(0), rho, rtol=1e-15)
+    np.testing.assert_allclose(np.einsum("q...,qa->...a", fs, s.lat.e),
+                               np.einsum("q...,qa->...a", f, s.lat.e), atol=1e-16)
