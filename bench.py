@@ -1,0 +1,303 @@
+#!/usr/bin/env python
+"""Benchmark: FP64 GLL node-updates/s of the SEM-LBM wetting step on B300.
+
+One "step" is one full time step of the method (collision + three SSP-RK3
+streaming stages, every kernel of the hot path) over the whole mesh.  Default
+workload: the 3D droplet on a sphere-cap wall, 16^3 curved hexes, N = 5,
+D3Q13, 884,736 element-local GLL nodes (synthetic mesh and tanh-initialised
+density; the paper's GMSH meshes are not available).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+Under torchrun each rank advances its own independent solve (the paper's
+sweeps are independent problems): weak scaling, no collective on the data
+path; the timing is bracketed by barriers and the max over ranks is taken.
+Prints one JSON line on rank 0.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2609_00535_b300 import flops as flopcount  # noqa: E402
+from paper_2609_00535_b300 import inputs  # noqa: E402
+
+METRIC = "FP64 GLL node-updates/s (3D droplet)"
+UNIT = "node-updates/s"
+L2_BYTES = 126 * 2 ** 20
+
+
+def make_case(name, ne=None):
+    if name == "sphere3d":
+        return inputs.sphere_3d(ne=(ne, ne, ne)) if ne else inputs.sphere_3d()
+    if name == "flat2d":
+        return inputs.flat_wall_2d()
+    if name == "cylinder2d":
+        return inputs.cylinder_2d()
+    raise SystemExit("unknown config %s" % name)
+
+
+def sample_case(name):
+    """Bounded sample of the workload for the CPU oracle: same mesh family, N,
+    velocity set and parameters, fewer elements."""
+    if name == "sphere3d":
+        return inputs.sphere_3d(ne=(4, 4, 4)), "sphere-cap mesh 4x4x4 elements, N=5, D3Q13 (13,824 nodes)"
+    if name == "flat2d":
+        return inputs.flat_wall_2d(), "the full 1,600-node mesh"
+    return inputs.cylinder_2d(n_theta=16, n_r=4), "cylinder O-grid 16x4 elements, N=6"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region (SM clock and throttle reasons)."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = max(float(r[2]) for r in rows if r[2].replace(".", "").isdigit())
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
+
+
+def oracle_rate(case, steps, warmup=0):
+    """Time the CPU oracle (as it stands) on a case: node-updates/s, threads."""
+    from tests.helpers import oracle_of
+    om, orc = oracle_of(case)
+    f = orc.initial_state(case.rho0.reshape(om.shape))
+    for _ in range(warmup):
+        f = orc.step(f)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        f = orc.step(f)
+    dt = time.perf_counter() - t0
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
+    except Exception:
+        cores = 1
+    return case.nodes * steps / dt, dt, cores
+
+
+def reference_arm(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    case, what = sample_case(args.config)
+    steps = max(1, args.steps)
+    rate, secs, cores = oracle_rate(case, steps, warmup=args.warmup)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "%s (oracle sample: %s)" % (args.config, what), "nodes": case.nodes},
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "%d steps of %s" % (steps, what)},
+        "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def native_arm(args):
+    import numpy as np
+    import torch
+    from paper_2609_00535_b300 import semlbm
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    device = local
+    torch.cuda.set_device(device)
+
+    case = make_case(args.config, args.ne)
+    solver = semlbm.Solver.from_case(case, device=device)
+    info = solver.info
+    solver.set_density(case.rho0)
+    stream = solver.stream
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    # warm-up (graph capture happens on the first step)
+    solver.step(args.warmup)
+    solver.synchronize()
+
+    # timed region: K steps, every kernel bracketed by CUDA events on the
+    # solver's stream (per-kernel durations for the roofline)
+    solver.profile(True)
+    clocks = Clocks(device)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        solver.step(1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    prof = solver.profile_read()
+    solver.profile(False)
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = info["n_local"] * args.steps * ws / (ms * 1e-3)
+    d = solver.diagnostics()
+
+    # roofline of the dominant kernel (k_rhs)
+    rhs_ms = prof["ms"]["k_rhs"] / max(prof["launches"]["k_rhs"], 1)
+    work = flopcount.rhs_work(case.lattice, case.mesh.N, info["n_local"], info["n_wall_nodes"])
+    peak, _ = semlbm.fp64_peak_tflops(device)
+    achieved = work["flops"] / (rhs_ms * 1e-3) / 1e12
+    total_kernel_ms = sum(prof["ms"].values())
+    shares = {k: round(v / total_kernel_ms, 4) for k, v in prof["ms"].items()}
+
+    # end to end through the public API with host buffers: every step uploads
+    # the state from pinned host memory, advances one step and reads the
+    # diagnostics back
+    Q, V = info["Q"], info["n_local"]
+    host = torch.empty(Q * V, dtype=torch.float64).pin_memory()
+    st, _ = solver.get_state()
+    host.copy_(torch.from_numpy(st.reshape(-1)))
+    e2e_steps = max(1, min(args.steps, 100))
+    solver.set_state(host, 0)
+    solver.step(1)
+    solver.diagnostics()
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        solver.set_state(host, 0)
+        solver.step(1)
+        solver.diagnostics()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if ws > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = V * e2e_steps * ws / e2e_s
+
+    line = None
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline:
+            cpu_steps = args.cpu_steps
+            rate, secs, cores = oracle_rate(case, cpu_steps)
+            cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                   "sample": "%d time steps of the full %s mesh (%d nodes), %.1f s" %
+                             (cpu_steps, args.config, case.nodes, secs)}
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {
+                "workload": args.config, "model": None,
+                "mesh": "%d curved hexes, N=%d" % (case.mesh.n_elem, case.mesh.N)
+                if case.mesh.dim == 3 else "%d quads, N=%d" % (case.mesh.n_elem, case.mesh.N),
+                "lattice": case.lattice, "nodes": V, "global_nodes": info["n_global"],
+                "dt": info["dt"], "tau": case.tau, "parallelism": "replicas" if ws > 1 else "1gpu",
+                "l2": "inputs larger than L2 (%.0f MB state+geometry vs 126 MB)" %
+                      (info["workspace_bytes"] / 1e6),
+            },
+            "roofline": {"bound": "alu", "kernel": "k_rhs", "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "peak_source": "measured live: FP64 DFMA probe (libsemlbm_peak)",
+                         "fp64_op_frac": work["ops"] / (rhs_ms * 1e-3) / (peak * 1e12 / 2),
+                         "kernel_ms": rhs_ms, "flops_per_launch": work["flops"]},
+            "kernel_share": shares,
+            "gpu_launches": int(sum(prof["launches"].values())),
+            "clocks": clk,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": Q * V * 8,
+                    "d2h_bytes_per_step": 80, "steps": e2e_steps},
+            "cpu_baseline": cpu,
+            "final_diag": {"ke_max": d["ke_max"], "mass": d["mass"], "status": d["status"]},
+        }
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--config", default="sphere3d", choices=["sphere3d", "flat2d", "cylinder2d"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-steps", type=int, default=3)
+    ap.add_argument("--ne", type=int, default=None,
+                    help="elements per axis of the sphere-cap mesh (profiling cases only)")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "native":
+        args.warmup = 3
+    if args.impl == "reference":
+        return reference_arm(args)
+    return native_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

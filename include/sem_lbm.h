@@ -1,0 +1,186 @@
+/*
+ * sem_lbm.h - C ABI of the B300 (sm_103a) FP64 spectral element lattice
+ * Boltzmann step for non-ideal gases with partial wetting.
+ *
+ * The method is that of "Spectral element lattice Boltzmann method for
+ * non-ideal gases with partial wetting boundary condition" (Zhao, Patel, Lee):
+ *   - chemical potential mu = mu0(rho) - kappa lap(rho), Eq. (chemi), with the
+ *     Laplacian in the weak form of Eq. (weak) whose wall integral carries the
+ *     wetting gradient n.grad(rho) = cos(theta) sqrt(2 e0/kappa) (Sec. 2.2);
+ *   - BGK collision with the higher-order force F** (Sec. 2.1, Appendix A);
+ *   - SSP-RK3 streaming in the weak form Eq. (advection)/(spetrum), force-split
+ *     as in Sec. 3.3, with the flux bounce-back wall flux J (Sec. 2.2, Eq. 9);
+ *   - direct-stiffness summation (gather-scatter) of every element-local
+ *     contribution across shared GLL nodes.
+ *
+ * Conventions common to every call
+ *   - Every function returns SEMLBM_OK (0) or a negative SEMLBM_E* code and,
+ *     on error, leaves a message readable with sem_lbm_last_error() (per
+ *     calling thread).  No call aborts the process.
+ *   - All floating-point data is IEEE binary64.
+ *   - Element-local node order: k = i + n j (+ n^2 l), n = N+1, i along the
+ *     first reference axis (fastest).  Faces: f = 2 b + s, b = reference axis,
+ *     s = 0 for xi_b = -1 and 1 for xi_b = +1.
+ *   - Field layout: scalar fields [E][n^d]; the state fbar [Q][E][n^d]
+ *     (structure of arrays per velocity).  Shared nodes are stored once per
+ *     element; the library keeps the copies equal.
+ *   - Velocity order.  D2Q9: 0 rest, 1 (1,0), 2 (0,1), 3 (-1,0), 4 (0,-1),
+ *     5 (1,1), 6 (-1,1), 7 (-1,-1), 8 (1,-1); weights 4/9, 1/9, 1/36.
+ *     D3Q13: 0 rest, then s*(0,1,phi), s*(0,-1,phi), s*(1,phi,0),
+ *     s*(-1,phi,0), s*(phi,0,1), s*(phi,0,-1) and e_{a+6} = -e_a, with
+ *     phi the golden ratio and |e| = sqrt(5/3); weights 2/5 and 1/20.
+ *     c_s^2 = 1/3 for both.
+ *   - Calls on one solver are not thread safe; distinct solvers are
+ *     independent.  Work is enqueued on the solver's stream (params.stream,
+ *     else a stream the solver owns).
+ */
+#ifndef SEM_LBM_H
+#define SEM_LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  SEMLBM_OK = 0,
+  SEMLBM_EINVAL = -1,      /* bad argument (null pointer, size, range, state) */
+  SEMLBM_ENOMEM = -2,      /* device memory or caller workspace too small     */
+  SEMLBM_ECUDA = -3,       /* a CUDA runtime call failed                       */
+  SEMLBM_ENONFINITE = -4,  /* the state holds NaN/Inf (diagnostics status)      */
+  SEMLBM_ETIMEOUT = -5,    /* a bounded device-side wait gave up                */
+  SEMLBM_EUNSUPPORTED = -6 /* order N or lattice/dimension pair not built       */
+};
+
+typedef enum { SEMLBM_D2Q9 = 0, SEMLBM_D3Q13 = 1 } sem_lbm_lattice;
+
+/* Mesh (host memory; copied by sem_lbm_create, the caller keeps ownership).
+ *   node_xyz  [n_elem][(N+1)^dim][dim]  GLL node coordinates of each element
+ *             (isoparametric: geometry order = N).  Elements must have a
+ *             positive Jacobian at every node.
+ *   global_id [n_elem][(N+1)^dim]  equal ids <=> the same mesh node (periodic
+ *             gluing is expressed by equal ids).  Any int64 values.
+ *   face_kind [n_elem][2 dim]  0 interior or periodic, 1 wall.
+ *   face_tag  [n_elem][2 dim]  wall contact-angle tag: < 0 neutral wall
+ *             (90 degrees), 0 -> theta_w, k >= 1 -> params->theta_tag[k-1]. */
+typedef struct {
+  int dim;
+  int64_t n_elem;
+  const double* node_xyz;
+  const int64_t* global_id;
+  const uint8_t* face_kind;
+  const int32_t* face_tag;
+} sem_lbm_mesh;
+
+/* Optional parameters; a zeroed struct (or a NULL pointer) gives defaults. */
+typedef struct {
+  double rho_l, rho_v;    /* phase densities (0 -> 1.0 and 0.1; Appendix A)       */
+  double dt;              /* time step; <= 0 -> min(cfl h_min / max|e_alpha|,
+                             0.1 h_min^2 / sqrt(rho_l kappa)), h_min the smallest
+                             distance between neighbouring GLL nodes              */
+  double cfl;             /* used when dt <= 0; 0 -> 0.4                            */
+  double mu0_factor;      /* mu0 = factor*beta(rho-rl)(rho-rv)(2rho-rl-rv); 0 -> 2  */
+  int n_tags;             /* entries in theta_tag                                   */
+  const double* theta_tag;/* contact angles (radians) of wall tags 1..n_tags        */
+  void* stream;           /* cudaStream_t to run on; NULL -> solver-owned stream    */
+  void* workspace;        /* caller device memory (e.g. from PyTorch) or NULL       */
+  size_t workspace_bytes; /* its size; must be >= sem_lbm_workspace_bytes()         */
+} sem_lbm_params;
+
+typedef struct sem_lbm sem_lbm_t;
+
+typedef struct {
+  int64_t step;       /* completed time steps                                  */
+  double time;        /* step * dt                                             */
+  double mass;        /* sum_e sum_i M_e,i rho_i (integral of rho)             */
+  double ke_max;      /* max over nodes of 0.5 rho |u|^2 (Sec. 3.3)           */
+  double ke_int;      /* integral of 0.5 rho |u|^2                             */
+  double umax;        /* max |u|                                               */
+  double rho_min, rho_max;
+  int64_t n_nonfinite;/* non-finite entries of fbar                            */
+  int status;         /* SEMLBM_OK or SEMLBM_ENONFINITE                        */
+} sem_lbm_diag;
+
+typedef struct {
+  int dim, N, Q;
+  int64_t n_elem, n_local;   /* n_local = n_elem (N+1)^dim                     */
+  int64_t n_global;          /* distinct global nodes                           */
+  int64_t n_wall_nodes;      /* element-local nodes on a wall face              */
+  double dt, kappa, beta, tau;
+  size_t workspace_bytes;
+  int graph_launches;        /* 1 if steps replay a captured CUDA graph         */
+  int kernels_per_step;      /* kernel launches in one time step                */
+} sem_lbm_info_t;
+
+/* Device bytes sem_lbm_create needs for this mesh (for admission control and
+ * for callers that pass their own workspace).  0 on invalid input. */
+size_t sem_lbm_workspace_bytes(const sem_lbm_mesh* mesh, int N, sem_lbm_lattice lattice);
+
+/* Build a solver: validates the mesh, builds GLL tables, the gather-scatter
+ * map and the wall records on the host, uploads the mesh and computes the
+ * geometry (Jacobians, metrics, masses, wall area vectors) in kernels.
+ *   N        polynomial order: 2..16 for D2Q9, 2..8 for D3Q13
+ *   beta     bulk free-energy coefficient of e0 = beta (rho-rl)^2 (rho-rv)^2
+ *   kappa    gradient-energy coefficient (Appendix A: beta delta^2 (rl-rv)^2/8)
+ *   tau      relaxation time in units of dt; collision rate 1/(tau + 1/2)
+ *   theta_w  contact angle (radians, measured through the liquid) of tag 0
+ * The state is undefined until sem_lbm_set_density or sem_lbm_set_state. */
+int sem_lbm_create(const sem_lbm_mesh* mesh, int N, sem_lbm_lattice lattice, double beta,
+                   double kappa, double tau, double theta_w, const sem_lbm_params* params,
+                   sem_lbm_t** out);
+
+/* fbar = f^eq(rho, u = 0) = t_alpha rho (Appendix A initial state).
+ * rho [n_elem][(N+1)^dim]; copies of a shared node must be equal. */
+int sem_lbm_set_density(sem_lbm_t* s, const double* rho, int rho_on_device);
+
+/* Advance n_steps >= 0 full time steps (collision + 3 SSP-RK3 stages).
+ * Asynchronous on the solver's stream; returns the launch status. */
+int sem_lbm_step(sem_lbm_t* s, int64_t n_steps);
+
+/* Reduce the diagnostics of the current state (synchronises the stream). */
+int sem_lbm_diagnostics(sem_lbm_t* s, sem_lbm_diag* out);
+
+/* Copy a field out.  which: 0 fbar [Q][E][n^d], 1 rho [E][n^d],
+ * 2 u [dim][E][n^d], 3 mu [E][n^d] (of the last computed stage-1 state).
+ * dst is host memory unless dst_on_device; host copies synchronise. */
+int sem_lbm_get_field(sem_lbm_t* s, int which, double* dst, int dst_on_device);
+
+/* Checkpoint: fbar [Q][E][n^d] plus the step counter. */
+int sem_lbm_get_state(sem_lbm_t* s, double* fbar, int on_device, int64_t* step);
+int sem_lbm_set_state(sem_lbm_t* s, const double* fbar, int on_device, int64_t step);
+
+int sem_lbm_get_info(const sem_lbm_t* s, sem_lbm_info_t* out);
+
+/* Per-kernel device timing, for measurement.  While enabled, sem_lbm_step
+ * issues the step's kernels directly (not as a graph replay) and records a
+ * CUDA event on the solver's stream after each launch, so that consecutive
+ * events bracket exactly one kernel.  sem_lbm_profile_read synchronises the
+ * stream and returns, per kernel class, the summed milliseconds and launch
+ * counts recorded since the last read (or since enabling), then resets them.
+ * Classes: 0 k_lap (weak Laplacian), 1 k_dss_mu (gather-scatter + mu),
+ * 2 k_force, 3 k_dss_collide (force average + collision), 4 k_rhs (streaming
+ * right-hand side), 5 k_dss_rk (gather-scatter + SSP-RK3 update). */
+#define SEMLBM_N_KERNEL_CLASSES 6
+typedef struct {
+  double ms[8];
+  int64_t launches[8];
+  double total_ms;    /* first to last event */
+} sem_lbm_profile_t;
+
+int sem_lbm_profile(sem_lbm_t* s, int enable);
+int sem_lbm_profile_read(sem_lbm_t* s, sem_lbm_profile_t* out);
+
+/* Releases device memory the solver allocated (never the caller's workspace)
+ * and the stream it owns.  NULL is ignored. */
+void sem_lbm_destroy(sem_lbm_t* s);
+
+/* Message of the calling thread's last failed call ("" if none). */
+const char* sem_lbm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SEM_LBM_H */

@@ -40,14 +40,11 @@ def d2q9():
 
 
 def d3q13():
+    """Rest + 12 icosahedron vertices, ordered so that e_{a+6} = -e_a (a = 1..6)."""
     phi = (1 + np.sqrt(5.0)) / 2
-    verts = []
-    for s1 in (1, -1):
-        for s2 in (1, -1):
-            verts.append((0, s1, s2 * phi))
-            verts.append((s1, s2 * phi, 0))
-            verts.append((s2 * phi, 0, s1))
-    verts = np.array(verts, dtype=np.float64)
+    half = np.array([(0, 1, phi), (0, -1, phi), (1, phi, 0), (-1, phi, 0), (phi, 0, 1),
+                     (phi, 0, -1)], dtype=np.float64)
+    verts = np.vstack([half, -half])
     verts *= np.sqrt(5 * CS2) / np.linalg.norm(verts[0])
     e = np.vstack([np.zeros((1, 3)), verts])
     t = np.array([2 / 5] + [1 / 20] * 12)

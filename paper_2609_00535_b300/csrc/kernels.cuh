@@ -1,0 +1,646 @@
+// FP64 kernels of the SEM-LBM time step (sm_103a).
+//
+// Element kernels (k_lap, k_force, k_rhs, k_geom): one CTA per batch of EPB
+// consecutive elements, one thread per element-local GLL node; the element
+// tiles of every field a kernel reads (rho, mu, the Q-1 moving f_alpha) and
+// the GLL derivative matrix are staged in shared memory, and each thread
+// applies the tensor-product (sum-factorised) derivative along each reference
+// axis with its rows of D held in registers.
+//
+// Gather-scatter kernels (k_dss_*): one thread per global node group; the
+// copies of a shared node are summed in a fixed order (ascending local index),
+// so results do not depend on scheduling.
+//
+// B300's FP64 pipe (about 1.1 TFLOP/s, measured) is the bound of this step, so
+// the formulation minimises FP64 instructions: velocity contractions use only
+// the non-zero components of e_alpha, opposite directions share their
+// coefficients, the rest population (e = 0) does not stream, and all index
+// arithmetic is integer.
+#pragma once
+#include <cstdint>
+
+#include "lattice.cuh"
+
+namespace semlbm {
+
+// threads of an element-kernel CTA: EPB elements of NP^D nodes, rounded to warps
+template <int D, int NP, int EPB>
+constexpr int cta_threads() { return ((EPB * ipow(NP, D) + 31) / 32) * 32; }
+
+struct WallDev {
+  const int* slot;     // [V]  wall record of an element-local node, or -1
+  const double* wet;   // [R]  sum over the node's wall faces: w_face |a| cos(theta) sqrt(2 beta/kappa)
+  const double* ae;    // [Q][R] sum over faces of w_face (a . e_alpha) where a . e_alpha < 0
+  int R;
+};
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+template <int D, int NP>
+struct NodeIdx {
+  int i[3];
+  __device__ __forceinline__ explicit NodeIdx(int k) {
+    i[0] = k % NP;
+    i[1] = (k / NP) % NP;
+    i[2] = (D == 3) ? k / (NP * NP) : 0;
+  }
+};
+
+// d/dxi_b of the element tile s (node k) with D row held in registers
+template <int NP, int STRIDE>
+__device__ __forceinline__ double dline(const double (&row)[NP], const double* __restrict__ line) {
+  double acc = row[0] * line[0];
+#pragma unroll
+  for (int m = 1; m < NP; ++m) acc = fma(row[m], line[m * STRIDE], acc);
+  return acc;
+}
+
+template <int D, int NP>
+__device__ __forceinline__ void grad_ref(const double (&Dr)[D][NP], const NodeIdx<D, NP>& ix,
+                                         const double* __restrict__ tile, int k, double (&out)[D]) {
+  out[0] = dline<NP, 1>(Dr[0], tile + k - ix.i[0]);
+  out[1] = dline<NP, NP>(Dr[1], tile + k - ix.i[1] * NP);
+  if constexpr (D == 3) out[2] = dline<NP, NP * NP>(Dr[2], tile + k - ix.i[2] * NP * NP);
+}
+
+template <int D, int NP>
+__device__ __forceinline__ void load_rows(const double* __restrict__ sD, const NodeIdx<D, NP>& ix,
+                                          bool transpose, double (&Dr)[D][NP]) {
+#pragma unroll
+  for (int b = 0; b < D; ++b)
+#pragma unroll
+    for (int m = 0; m < NP; ++m)
+      Dr[b][m] = transpose ? sD[m * NP + ix.i[b]] : sD[ix.i[b] * NP + m];
+}
+
+__device__ __forceinline__ void stage_in(double* __restrict__ s, const double* __restrict__ g,
+                                         int64_t base, int count) {
+  for (int i = threadIdx.x; i < count; i += blockDim.x) s[i] = __ldg(g + base + i);
+}
+
+__device__ __forceinline__ bool nonfinite(double x) {
+  return ((__double_as_longlong(x) >> 52) & 0x7ff) == 0x7ff;
+}
+
+// ---------------------------------------------------------------------------
+// setup: geometry per node (Jacobian by D on the coordinates), Eq. (spetrum) M
+// ---------------------------------------------------------------------------
+template <int D, int NP, int EPB>
+__global__ void __launch_bounds__(cta_threads<D, NP, EPB>()) k_geom(const double* __restrict__ xyz, const double* __restrict__ Dmat,
+                       const double* __restrict__ wgll, double* __restrict__ Jinv,
+                       double* __restrict__ Gm, double* __restrict__ Me, int* __restrict__ bad,
+                       int64_t V, int E) {
+  constexpr int NL = ipow(NP, D), NT = EPB * NL;
+  extern __shared__ double sm[];
+  double* sD = sm;
+  double* sx = sD + NP * NP;   // [D][NT]
+  const int e0 = blockIdx.x * EPB;
+  const int count = min(EPB, E - e0) * NL;
+  const int64_t base = (int64_t)e0 * NL;
+  for (int i = threadIdx.x; i < NP * NP; i += blockDim.x) sD[i] = Dmat[i];
+  for (int i = threadIdx.x; i < count * D; i += blockDim.x) {
+    const int node = i / D, a = i - node * D;
+    sx[a * NT + node] = xyz[(base + node) * D + a];
+  }
+  __syncthreads();
+  const int tid = threadIdx.x;
+  if (tid >= count) return;
+  const int le = tid / NL, k = tid - le * NL;
+  const NodeIdx<D, NP> ix(k);
+  double Dr[D][NP];
+  load_rows<D, NP>(sD, ix, false, Dr);
+  double J[3][3] = {};
+  for (int a = 0; a < D; ++a) {
+    double g[D];
+    grad_ref<D, NP>(Dr, ix, sx + a * NT + le * NL, k, g);
+    for (int b = 0; b < D; ++b) J[a][b] = g[b];        // J[a][b] = dx_a / dxi_b
+  }
+  double adj[3][3], det;
+  if constexpr (D == 2) {
+    adj[0][0] = J[1][1]; adj[0][1] = -J[0][1];
+    adj[1][0] = -J[1][0]; adj[1][1] = J[0][0];
+    det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+  } else {
+    // row b of adj(J) = (column c) x (column d), (b, c, d) cyclic
+    for (int b = 0; b < 3; ++b) {
+      const int c = (b + 1) % 3, d = (b + 2) % 3;
+      adj[b][0] = J[1][c] * J[2][d] - J[2][c] * J[1][d];
+      adj[b][1] = J[2][c] * J[0][d] - J[0][c] * J[2][d];
+      adj[b][2] = J[0][c] * J[1][d] - J[1][c] * J[0][d];
+    }
+    det = J[0][0] * adj[0][0] + J[1][0] * adj[0][1] + J[2][0] * adj[0][2];
+  }
+  if (!(det > 0.0)) atomicOr(bad, 1);
+  const double inv = 1.0 / det;
+  const int64_t idx = base + tid;
+  double Ji[3][3];
+  for (int b = 0; b < D; ++b)
+    for (int a = 0; a < D; ++a) {
+      Ji[b][a] = adj[b][a] * inv;                        // dxi_b / dx_a
+      Jinv[(b * D + a) * V + idx] = Ji[b][a];
+    }
+  double W = wgll[ix.i[0]] * wgll[ix.i[1]];
+  if constexpr (D == 3) W *= wgll[ix.i[2]];
+  const double me = W * det;
+  Me[idx] = me;
+  int p = 0;
+  for (int b = 0; b < D; ++b)
+    for (int c = b; c < D; ++c) {
+      double s = 0.0;
+      for (int a = 0; a < D; ++a) s += Ji[b][a] * Ji[c][a];
+      Gm[(p++) * V + idx] = me * s;
+    }
+}
+
+// assembled mass: invMg[g] = 1 / sum over copies of M_e
+__global__ void k_dss_mass(const int* __restrict__ off, const int* __restrict__ idx, int G,
+                           const double* __restrict__ Me, double* __restrict__ invMg) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= G) return;
+  double s = 0.0;
+  for (int j = off[g]; j < off[g + 1]; ++j) s += Me[idx[j]];
+  invMg[g] = 1.0 / s;
+}
+
+// wall records: area vector of each wall face at the node (cofactor row of J
+// times the face's GLL weights, outward), summed over the node's wall faces
+template <class L, int NP>
+__global__ void k_wall_setup(const double* __restrict__ xyz, const double* __restrict__ Dmat,
+                             const double* __restrict__ wgll, const int* __restrict__ rec_elem,
+                             const int* __restrict__ rec_node, const double* __restrict__ rec_cos,
+                             const int* __restrict__ rec_mask, int R, double sq2bk,
+                             double* __restrict__ wet, double* __restrict__ ae) {
+  constexpr int D = L::D, NL = ipow(NP, D);
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  const int e = rec_elem[r], k = rec_node[r], mask = rec_mask[r];
+  const NodeIdx<D, NP> ix(k);
+  const double* X = xyz + (int64_t)e * NL * D;
+  const int stride[3] = {1, NP, NP * NP};
+  double J[3][3] = {};
+  for (int a = 0; a < D; ++a)
+    for (int b = 0; b < D; ++b) {
+      double s = 0.0;
+      const int k0 = k - ix.i[b] * stride[b];
+      for (int m = 0; m < NP; ++m) s += Dmat[ix.i[b] * NP + m] * X[(k0 + m * stride[b]) * D + a];
+      J[a][b] = s;
+    }
+  double adj[3][3];
+  if constexpr (D == 2) {
+    adj[0][0] = J[1][1]; adj[0][1] = -J[0][1];
+    adj[1][0] = -J[1][0]; adj[1][1] = J[0][0];
+  } else {
+    for (int b = 0; b < 3; ++b) {
+      const int c = (b + 1) % 3, d = (b + 2) % 3;
+      adj[b][0] = J[1][c] * J[2][d] - J[2][c] * J[1][d];
+      adj[b][1] = J[2][c] * J[0][d] - J[0][c] * J[2][d];
+      adj[b][2] = J[0][c] * J[1][d] - J[1][c] * J[0][d];
+    }
+  }
+  double wsum = 0.0;
+  double acc[L::Q];
+  for (int q = 0; q < L::Q; ++q) acc[q] = 0.0;
+  for (int f = 0; f < 2 * D; ++f) {
+    if (!((mask >> f) & 1)) continue;
+    const int b = f >> 1;
+    const double sgn = (f & 1) ? 1.0 : -1.0;
+    double wf = 1.0;
+    for (int c = 0; c < D; ++c)
+      if (c != b) wf *= wgll[ix.i[c]];
+    double a[3], an = 0.0;
+    for (int c = 0; c < D; ++c) {
+      a[c] = sgn * adj[b][c] * wf;
+      an += a[c] * a[c];
+    }
+    an = sqrt(an);
+    wsum += an * rec_cos[r * 2 * D + f] * sq2bk;
+    for (int q = 1; q < L::Q; ++q) {
+      double dot = 0.0;
+      for (int c = 0; c < D; ++c) dot += L::C(q, c) * a[c];
+      dot *= L::S;
+      // tangential directions (a . e = 0 up to rounding) are not incoming
+      if (dot < -1e-13 * an * L::SPEED_MAX) acc[q] += dot;
+    }
+  }
+  wet[r] = wsum;
+  for (int q = 0; q < L::Q; ++q) ae[(int64_t)q * R + r] = acc[q];
+}
+
+// ---------------------------------------------------------------------------
+// a2: element-local weak Laplacian with the wetting wall term, Eq. (weak)
+//     r_i = -sum_b D^T_b [ sum_c G_bc d_c rho ] + wall_i ws cos(theta) sqrt(2b/k)(rl-rho)(rho-rv)
+// ---------------------------------------------------------------------------
+template <class L, int NP, int EPB>
+__global__ void __launch_bounds__(cta_threads<L::D, NP, EPB>()) k_lap(const double* __restrict__ rho, const double* __restrict__ Gm, WallDev w,
+                      const double* __restrict__ Dmat, double rho_l, double rho_v,
+                      double* __restrict__ out, int64_t V, int E) {
+  constexpr int D = L::D, NL = ipow(NP, D), NT = EPB * NL;
+  extern __shared__ double sm[];
+  double* sD = sm;
+  double* sr = sD + NP * NP;
+  double* st = sr + NT;     // [D][NT]
+  const int e0 = blockIdx.x * EPB;
+  const int count = min(EPB, E - e0) * NL;
+  const int64_t base = (int64_t)e0 * NL;
+  for (int i = threadIdx.x; i < NP * NP; i += blockDim.x) sD[i] = Dmat[i];
+  stage_in(sr, rho, base, count);
+  __syncthreads();
+  const int tid = threadIdx.x;
+  const bool act = tid < count;
+  const int le = tid / NL, k = tid - le * NL;
+  const NodeIdx<D, NP> ix(act ? k : 0);
+  const int64_t idx = base + tid;
+  if (act) {
+    double Dr[D][NP];
+    load_rows<D, NP>(sD, ix, false, Dr);
+    double g[D];
+    grad_ref<D, NP>(Dr, ix, sr + le * NL, k, g);
+    if constexpr (D == 2) {
+      const double g00 = Gm[idx], g01 = Gm[V + idx], g11 = Gm[2 * V + idx];
+      st[tid] = fma(g01, g[1], g00 * g[0]);
+      st[NT + tid] = fma(g11, g[1], g01 * g[0]);
+    } else {
+      const double g00 = Gm[idx], g01 = Gm[V + idx], g02 = Gm[2 * V + idx];
+      const double g11 = Gm[3 * V + idx], g12 = Gm[4 * V + idx], g22 = Gm[5 * V + idx];
+      st[tid] = fma(g02, g[2], fma(g01, g[1], g00 * g[0]));
+      st[NT + tid] = fma(g12, g[2], fma(g11, g[1], g01 * g[0]));
+      st[2 * NT + tid] = fma(g22, g[2], fma(g12, g[1], g02 * g[0]));
+    }
+  }
+  __syncthreads();
+  if (!act) return;
+  double Dt[D][NP];
+  load_rows<D, NP>(sD, ix, true, Dt);
+  const int lb = le * NL;
+  double acc = dline<NP, 1>(Dt[0], st + lb + k - ix.i[0]);
+  acc += dline<NP, NP>(Dt[1], st + NT + lb + k - ix.i[1] * NP);
+  if constexpr (D == 3) acc += dline<NP, NP * NP>(Dt[2], st + 2 * NT + lb + k - ix.i[2] * NP * NP);
+  double r = -acc;
+  const int slot = w.slot[idx];
+  if (slot >= 0) {
+    const double rh = sr[lb + k];
+    r = fma(w.wet[slot], (rho_l - rh) * (rh - rho_v), r);
+  }
+  out[idx] = r;
+}
+
+// a3: DSS of the Laplacian partials and the chemical potential, Eq. (chemi)
+__global__ void k_dss_mu(const int* __restrict__ off, const int* __restrict__ idx, int G,
+                         const double* __restrict__ lapr, const double* __restrict__ rho,
+                         const double* __restrict__ invMg, double fbeta, double rho_l,
+                         double rho_v, double kappa, double* __restrict__ mu) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= G) return;
+  const int j0 = off[g], j1 = off[g + 1];
+  const int i0 = idx[j0];
+  double s = lapr[i0];
+  for (int j = j0 + 1; j < j1; ++j) s += lapr[idx[j]];
+  const double lap = s * invMg[g];
+  const double r = rho[i0];
+  const double m0 = fbeta * (r - rho_l) * (r - rho_v) * (2.0 * r - rho_l - rho_v);
+  const double val = fma(-kappa, lap, m0);
+  for (int j = j0; j < j1; ++j) mu[idx[j]] = val;
+}
+
+// a4 (part 1): element-local force M_e (c_s^2 grad rho - rho grad mu) (Sec. 2.1)
+template <class L, int NP, int EPB>
+__global__ void __launch_bounds__(cta_threads<L::D, NP, EPB>()) k_force(const double* __restrict__ rho, const double* __restrict__ mu,
+                        const double* __restrict__ Jinv, const double* __restrict__ Me,
+                        const double* __restrict__ Dmat, double* __restrict__ Fp, int64_t V,
+                        int E) {
+  constexpr int D = L::D, NL = ipow(NP, D), NT = EPB * NL;
+  extern __shared__ double sm[];
+  double* sD = sm;
+  double* sr = sD + NP * NP;
+  double* smu = sr + NT;
+  const int e0 = blockIdx.x * EPB;
+  const int count = min(EPB, E - e0) * NL;
+  const int64_t base = (int64_t)e0 * NL;
+  for (int i = threadIdx.x; i < NP * NP; i += blockDim.x) sD[i] = Dmat[i];
+  stage_in(sr, rho, base, count);
+  stage_in(smu, mu, base, count);
+  __syncthreads();
+  const int tid = threadIdx.x;
+  if (tid >= count) return;
+  const int le = tid / NL, k = tid - le * NL;
+  const NodeIdx<D, NP> ix(k);
+  const int64_t idx = base + tid;
+  double Dr[D][NP];
+  load_rows<D, NP>(sD, ix, false, Dr);
+  double dr[D], dm[D];
+  grad_ref<D, NP>(Dr, ix, sr + le * NL, k, dr);
+  grad_ref<D, NP>(Dr, ix, smu + le * NL, k, dm);
+  const double rh = sr[le * NL + k];
+  const double me = Me[idx];
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    double gr = 0.0, gm = 0.0;
+#pragma unroll
+    for (int b = 0; b < D; ++b) {
+      const double j = Jinv[(b * D + a) * V + idx];
+      gr = (b == 0) ? j * dr[b] : fma(j, dr[b], gr);
+      gm = (b == 0) ? j * dm[b] : fma(j, dm[b], gm);
+    }
+    Fp[a * V + idx] = me * fma(kCs2, gr, -rh * gm);
+  }
+}
+
+// a4 (part 2): DSS average of the force and BGK collision with F**
+//   f* = fbar - (fbar - fbar_eq)/(tau + 1/2) + dt F**, fbar_eq = f^eq - dt F**/2
+template <class L>
+__global__ void k_dss_collide(const int* __restrict__ off, const int* __restrict__ idx, int G,
+                              const double* __restrict__ Fp, const double* __restrict__ invMg,
+                              const double* __restrict__ f, const double* __restrict__ rho,
+                              double omega, double dt, double* __restrict__ fs, int64_t V) {
+  constexpr int D = L::D, Q = L::Q;
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= G) return;
+  const int j0 = off[g], j1 = off[g + 1];
+  const int i0 = idx[j0];
+  const double im = invMg[g];
+  double F[D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    double s = Fp[a * V + i0];
+    for (int j = j0 + 1; j < j1; ++j) s += Fp[a * V + idx[j]];
+    F[a] = s * im;
+  }
+  double fa[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) fa[q] = f[q * V + i0];
+  const double rh = rho[i0];
+  // rho u = sum_a fbar_a e_a (Eq. momentum), via opposite-direction differences
+  double m[D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) m[a] = 0.0;
+  static_for<0, L::NREP>([&](auto R) {
+    constexpr int A = L::rep(decltype(R)::value), B = L::opp(A);
+    const double dfa = fa[A] - fa[B];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const double c = L::C(A, a);
+      if (c == 1.0) m[a] += dfa;
+      else if (c == -1.0) m[a] -= dfa;
+      else if (c != 0.0) m[a] = fma(c, dfa, m[a]);
+    }
+  });
+  const double su = L::S / rh;
+  double u[D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) u[a] = m[a] * su;
+  double uu = u[0] * u[0], uF = u[0] * F[0];
+#pragma unroll
+  for (int a = 1; a < D; ++a) {
+    uu = fma(u[a], u[a], uu);
+    uF = fma(u[a], F[a], uF);
+  }
+  const double base_eq = fma(-1.5, uu, 1.0);   // 1 - u^2/(2 c_s^2)
+  const double hdt = 0.5 * dt;
+  auto relax = [&](double fv, double t, double eu, double eF) {
+    // f^eq (Eq. geq_s) and F** (Sec. 2.1) with c_s^2 = 1/3
+    const double feq = rh * t * fma(eu, fma(4.5, eu, 3.0), base_eq);
+    const double fss = 3.0 * t * fma(3.0 * eu, eF, -uF);
+    const double fbeq = fma(-hdt, fss, feq);
+    return fma(dt, fss, fma(-omega, fv - fbeq, fv));
+  };
+  double out[Q];
+  out[0] = relax(fa[0], L::t(0), 0.0, 0.0);
+  static_for<0, L::NREP>([&](auto R) {
+    constexpr int A = L::rep(decltype(R)::value), B = L::opp(A);
+    const double eu = L::S * L::template cdot<A>(u);
+    const double eF = L::S * L::template cdot<A>(F);
+    out[A] = relax(fa[A], L::t(A), eu, eF);
+    out[B] = relax(fa[B], L::t(A), -eu, -eF);
+  });
+  for (int j = j0; j < j1; ++j) {
+    const int ii = idx[j];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) fs[q * V + ii] = out[q];
+  }
+}
+
+// a5: element-local right-hand side of the force-split streaming (Sec. 3.3)
+//   r_a = M_e [ -e_a . grad(g_a - t_a rho) - (t_a/c_s^2) rho e_a . grad(mu) ]
+//         + flux bounce-back on incoming wall directions (Sec. 2.2)
+template <class L, int NP, int EPB>
+__global__ void __launch_bounds__(cta_threads<L::D, NP, EPB>()) k_rhs(const double* __restrict__ gst, const double* __restrict__ rho,
+                      const double* __restrict__ mu, const double* __restrict__ Jinv,
+                      const double* __restrict__ Me, WallDev w, const double* __restrict__ Dmat,
+                      double* __restrict__ r, int64_t V, int E) {
+  constexpr int D = L::D, Q = L::Q, NL = ipow(NP, D), NT = EPB * NL;
+  extern __shared__ double sm[];
+  double* sD = sm;
+  double* sr = sD + NP * NP;
+  double* smu = sr + NT;
+  double* sg = smu + NT;   // [Q-1][NT], moving directions only
+  const int e0 = blockIdx.x * EPB;
+  const int count = min(EPB, E - e0) * NL;
+  const int64_t base = (int64_t)e0 * NL;
+  for (int i = threadIdx.x; i < NP * NP; i += blockDim.x) sD[i] = Dmat[i];
+  stage_in(sr, rho, base, count);
+  stage_in(smu, mu, base, count);
+#pragma unroll 1
+  for (int q = 1; q < Q; ++q) stage_in(sg + (q - 1) * NT, gst + q * V, base, count);
+  __syncthreads();
+  const int tid = threadIdx.x;
+  if (tid >= count) return;
+  const int le = tid / NL, k = tid - le * NL, lb = le * NL;
+  const NodeIdx<D, NP> ix(k);
+  const int64_t idx = base + tid;
+  double Dr[D][NP];
+  load_rows<D, NP>(sD, ix, false, Dr);
+  double dr[D], dm[D];
+  grad_ref<D, NP>(Dr, ix, sr + lb, k, dr);
+  grad_ref<D, NP>(Dr, ix, smu + lb, k, dm);
+  const double rh3 = kInvCs2 * sr[lb + k];
+  double v[D];   // d_b rho - (rho / c_s^2) d_b mu, reference components
+#pragma unroll
+  for (int b = 0; b < D; ++b) v[b] = fma(-rh3, dm[b], dr[b]);
+  double J[D][D];
+#pragma unroll
+  for (int b = 0; b < D; ++b)
+#pragma unroll
+    for (int a = 0; a < D; ++a) J[b][a] = Jinv[(b * D + a) * V + idx];
+  const double ms = Me[idx] * L::S;
+  const int slot = w.slot[idx];
+  static_for<0, L::NREP>([&](auto R) {
+    constexpr int A = L::rep(decltype(R)::value), B = L::opp(A);
+    constexpr double T = L::t(A);
+    double c[D];   // (J^-1 C_A)_b: e_A . grad = S sum_b c_b d_b
+#pragma unroll
+    for (int b = 0; b < D; ++b) c[b] = L::template cdot<A>(J[b]);
+    double dg[D];
+    grad_ref<D, NP>(Dr, ix, sg + (A - 1) * NT + lb, k, dg);
+    double s = c[0] * fma(T, v[0], -dg[0]);
+#pragma unroll
+    for (int b = 1; b < D; ++b) s = fma(c[b], fma(T, v[b], -dg[b]), s);
+    double rA = ms * s;
+    grad_ref<D, NP>(Dr, ix, sg + (B - 1) * NT + lb, k, dg);
+    s = c[0] * fma(T, v[0], -dg[0]);
+#pragma unroll
+    for (int b = 1; b < D; ++b) s = fma(c[b], fma(T, v[b], -dg[b]), s);
+    double rB = -ms * s;
+    if (slot >= 0) {
+      const double gA = sg[(A - 1) * NT + lb + k], gB = sg[(B - 1) * NT + lb + k];
+      rA = fma(w.ae[(int64_t)A * w.R + slot], gA - gB, rA);
+      rB = fma(w.ae[(int64_t)B * w.R + slot], gB - gA, rB);
+    }
+    r[A * V + idx] = rA;
+    r[B * V + idx] = rB;
+  });
+}
+
+// a5 (part 2): DSS of the right-hand side, M^-1, and the SSP-RK3 stage update
+//   stage 1: U1 = U0 + dt L;  stage 2: U2 = 3/4 U0 + 1/4 (U1 + dt L);
+//   stage 3: f^{n+1} = 1/3 U0 + 2/3 (U2 + dt L); rho of the new state
+template <class L, int STAGE>
+__global__ void k_dss_rk(const int* __restrict__ off, const int* __restrict__ idx, int G,
+                         const double* __restrict__ r, const double* __restrict__ invMg,
+                         const double* __restrict__ U0, const double* __restrict__ gcur,
+                         double dt, double* __restrict__ out, double* __restrict__ rho,
+                         int* __restrict__ flag, int64_t V) {
+  constexpr int Q = L::Q;
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= G) return;
+  const int j0 = off[g], j1 = off[g + 1];
+  const int i0 = idx[j0];
+  const double im = invMg[g];
+  double val[Q];
+  double rs = 0.0;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    double Lq = 0.0;
+    if (q > 0) {
+      double s = r[q * V + i0];
+      for (int j = j0 + 1; j < j1; ++j) s += r[q * V + idx[j]];
+      Lq = s * im;
+    }
+    const double u0 = U0[q * V + i0];
+    double v;
+    if constexpr (STAGE == 1) {
+      v = fma(dt, Lq, u0);
+    } else if constexpr (STAGE == 2) {
+      v = fma(0.25, fma(dt, Lq, gcur[q * V + i0]), 0.75 * u0);
+    } else {
+      v = fma(2.0 / 3.0, fma(dt, Lq, gcur[q * V + i0]), u0 * (1.0 / 3.0));
+    }
+    val[q] = v;
+    rs += v;
+  }
+  if (nonfinite(rs)) atomicOr(flag, 1);
+  for (int j = j0; j < j1; ++j) {
+    const int ii = idx[j];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) out[q * V + ii] = val[q];
+    rho[ii] = rs;
+  }
+}
+
+// a6: diagnostics (Sec. 3.3 KE_max), deterministic two-pass reduction
+struct DiagPart {
+  double mass, ke_int, ke_max, u2max, rho_min, rho_max, nonfinite;
+};
+
+template <class L>
+__global__ void k_diag(const double* __restrict__ f, const double* __restrict__ Me,
+                       DiagPart* __restrict__ part, int64_t V) {
+  constexpr int D = L::D, Q = L::Q;
+  __shared__ DiagPart sh[256];
+  DiagPart p = {0.0, 0.0, 0.0, 0.0, 1e300, -1e300, 0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < V;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double fa[Q];
+    double rh = 0.0;
+    for (int q = 0; q < Q; ++q) {
+      fa[q] = f[q * V + i];
+      rh += fa[q];
+      if (nonfinite(fa[q])) p.nonfinite += 1.0;
+    }
+    double u2 = 0.0;
+    for (int a = 0; a < D; ++a) {
+      double m = 0.0;
+      for (int q = 1; q < Q; ++q) m += L::C(q, a) * fa[q];
+      const double u = m * L::S / rh;
+      u2 += u * u;
+    }
+    const double ke = 0.5 * rh * u2;
+    const double me = Me[i];
+    p.mass += me * rh;
+    p.ke_int += me * ke;
+    p.ke_max = fmax(p.ke_max, ke);
+    p.u2max = fmax(p.u2max, u2);
+    p.rho_min = fmin(p.rho_min, rh);
+    p.rho_max = fmax(p.rho_max, rh);
+  }
+  sh[threadIdx.x] = p;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      DiagPart& a = sh[threadIdx.x];
+      const DiagPart& b = sh[threadIdx.x + s];
+      a.mass += b.mass;
+      a.ke_int += b.ke_int;
+      a.ke_max = fmax(a.ke_max, b.ke_max);
+      a.u2max = fmax(a.u2max, b.u2max);
+      a.rho_min = fmin(a.rho_min, b.rho_min);
+      a.rho_max = fmax(a.rho_max, b.rho_max);
+      a.nonfinite += b.nonfinite;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void k_diag_final(const DiagPart* __restrict__ part, int n, DiagPart* __restrict__ out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  DiagPart a = part[0];
+  for (int i = 1; i < n; ++i) {
+    const DiagPart& b = part[i];
+    a.mass += b.mass;
+    a.ke_int += b.ke_int;
+    a.ke_max = fmax(a.ke_max, b.ke_max);
+    a.u2max = fmax(a.u2max, b.u2max);
+    a.rho_min = fmin(a.rho_min, b.rho_min);
+    a.rho_max = fmax(a.rho_max, b.rho_max);
+    a.nonfinite += b.nonfinite;
+  }
+  *out = a;
+}
+
+// initial state fbar = t_a rho (f^eq at u = 0)
+template <class L>
+__global__ void k_init(const double* __restrict__ rho_in, double* __restrict__ f,
+                       double* __restrict__ rho, int64_t V) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= V) return;
+  const double r = rho_in[i];
+  rho[i] = r;
+  for (int q = 0; q < L::Q; ++q) f[q * V + i] = L::t(q) * r;
+}
+
+// rho = sum_a fbar_a (after set_state)
+template <class L>
+__global__ void k_density(const double* __restrict__ f, double* __restrict__ rho, int64_t V) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= V) return;
+  double s = 0.0;
+  for (int q = 0; q < L::Q; ++q) s += f[q * V + i];
+  rho[i] = s;
+}
+
+// u = sum_a fbar_a e_a / rho, [D][V]
+template <class L>
+__global__ void k_velocity(const double* __restrict__ f, double* __restrict__ u, int64_t V) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= V) return;
+  double rh = 0.0;
+  for (int q = 0; q < L::Q; ++q) rh += f[q * V + i];
+  for (int a = 0; a < L::D; ++a) {
+    double m = 0.0;
+    for (int q = 1; q < L::Q; ++q) m += L::C(q, a) * f[q * V + i];
+    u[a * V + i] = m * L::S / rh;
+  }
+}
+
+}  // namespace semlbm

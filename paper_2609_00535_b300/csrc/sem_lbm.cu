@@ -1,0 +1,754 @@
+// Host side of libsemlbm: setup tables, gather-scatter map, wall records,
+// workspace layout, kernel dispatch and the C ABI declared in sem_lbm.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "kernels.cuh"
+#include "sem_lbm.h"
+
+using namespace semlbm;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define CUDA_TRY(expr)                                                                    \
+  do {                                                                                    \
+    cudaError_t e_ = (expr);                                                              \
+    if (e_ != cudaSuccess) return fail(SEMLBM_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// GLL tables in long double.  Nodes: Newton on P_{N+1} - P_{N-1}, whose zeros
+// are +-1 and the zeros of P_N' and whose derivative is (2N+1) P_N.  Weights
+// 2 / (N(N+1) P_N(x)^2).  Derivative matrix: the GLL closed form
+// D_ij = P_N(x_i) / (P_N(x_j)(x_i - x_j)), D_00 = -N(N+1)/4, D_NN = N(N+1)/4.
+// ---------------------------------------------------------------------------
+void legendre_ld(int n, long double x, long double* p) {  // p[0..n]
+  p[0] = 1.0L;
+  if (n >= 1) p[1] = x;
+  for (int k = 1; k < n; ++k) p[k + 1] = ((2 * k + 1) * x * p[k] - k * p[k - 1]) / (k + 1);
+}
+
+void gll_tables(int N, std::vector<double>& x, std::vector<double>& w, std::vector<double>& D) {
+  const int n = N + 1;
+  std::vector<long double> xl(n), pN(n), p(N + 2);
+  for (int j = 0; j < n; ++j) {
+    long double xj = -cosl(3.14159265358979323846264338327950288L * j / N);
+    if (j > 0 && j < N) {
+      for (int it = 0; it < 100; ++it) {
+        legendre_ld(N + 1, xj, p.data());
+        const long double f = p[N + 1] - p[N - 1];
+        const long double df = (2 * N + 1) * p[N];
+        const long double dx = f / df;
+        xj -= dx;
+        if (fabsl(dx) < 1e-30L) break;
+      }
+    }
+    xl[j] = xj;
+    legendre_ld(N, xj, p.data());
+    pN[j] = p[N];
+  }
+  x.resize(n);
+  w.resize(n);
+  D.assign(n * n, 0.0);
+  for (int j = 0; j < n; ++j) {
+    x[j] = (double)xl[j];
+    w[j] = (double)(2.0L / ((long double)N * (N + 1) * pN[j] * pN[j]));
+  }
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      long double v;
+      if (i != j) v = pN[i] / (pN[j] * (xl[i] - xl[j]));
+      else if (i == 0) v = -(long double)N * (N + 1) / 4;
+      else if (i == N) v = (long double)N * (N + 1) / 4;
+      else v = 0.0L;
+      D[i * n + j] = (double)v;
+    }
+}
+
+size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
+
+struct HostMaps {
+  std::vector<int> off, idx;          // gather-scatter CSR (groups by first copy)
+  std::vector<int> slot;              // [V] wall record or -1
+  std::vector<int> rec_elem, rec_node, rec_mask;
+  std::vector<double> rec_cos;        // [R][2D]
+  int64_t G = 0;
+};
+
+int build_maps(const sem_lbm_mesh* m, int N, double theta_w, const sem_lbm_params* p,
+               HostMaps& h) {
+  const int D = m->dim, n = N + 1;
+  int NL = 1;
+  for (int a = 0; a < D; ++a) NL *= n;
+  const int64_t E = m->n_elem, V = E * NL;
+  // gather-scatter groups: sort (global id, local index)
+  std::vector<std::pair<int64_t, int>> key(V);
+  for (int64_t i = 0; i < V; ++i) key[i] = {m->global_id[i], (int)i};
+  std::sort(key.begin(), key.end());
+  std::vector<std::pair<int, int>> grp;   // (first local index, start in key)
+  for (int64_t i = 0; i < V; ++i)
+    if (i == 0 || key[i].first != key[i - 1].first) grp.push_back({key[i].second, (int)i});
+  std::sort(grp.begin(), grp.end());
+  h.G = (int64_t)grp.size();
+  h.off.resize(h.G + 1);
+  h.idx.resize(V);
+  int pos = 0;
+  for (int64_t g = 0; g < h.G; ++g) {
+    h.off[g] = pos;
+    for (int64_t i = grp[g].second; i < V && key[i].first == key[grp[g].second].first; ++i)
+      h.idx[pos++] = key[i].second;
+  }
+  h.off[h.G] = pos;
+  // wall records: one per element-local node that lies on a wall face
+  auto cos_of = [&](int tag, double* c) -> int {
+    if (tag < 0) { *c = 0.0; return 0; }
+    if (tag == 0) { *c = std::cos(theta_w); return 0; }
+    if (!p || tag > p->n_tags || !p->theta_tag)
+      return fail(SEMLBM_EINVAL, "wall tag %d has no contact angle (n_tags = %d)", tag,
+                  p ? p->n_tags : 0);
+    *c = std::cos(p->theta_tag[tag - 1]);
+    return 0;
+  };
+  h.slot.assign(V, -1);
+  std::vector<int> mask(NL);
+  std::vector<double> cosf(2 * D);
+  for (int64_t e = 0; e < E; ++e) {
+    bool any = false;
+    for (int f = 0; f < 2 * D; ++f) {
+      const uint8_t k = m->face_kind[e * 2 * D + f];
+      if (k > 1) return fail(SEMLBM_EINVAL, "face_kind must be 0 or 1 (element %lld)", (long long)e);
+      if (k == 1) {
+        any = true;
+        if (int rc = cos_of(m->face_tag[e * 2 * D + f], &cosf[f])) return rc;
+      } else {
+        cosf[f] = 0.0;
+      }
+    }
+    if (!any) continue;
+    std::fill(mask.begin(), mask.end(), 0);
+    for (int f = 0; f < 2 * D; ++f) {
+      if (m->face_kind[e * 2 * D + f] != 1) continue;
+      const int b = f >> 1, side = (f & 1) ? N : 0;
+      for (int k = 0; k < NL; ++k) {
+        const int ib = (b == 0) ? k % n : (b == 1 ? (k / n) % n : k / (n * n));
+        if (ib == side) mask[k] |= 1 << f;
+      }
+    }
+    for (int k = 0; k < NL; ++k) {
+      if (!mask[k]) continue;
+      h.slot[e * NL + k] = (int)h.rec_elem.size();
+      h.rec_elem.push_back((int)e);
+      h.rec_node.push_back(k);
+      h.rec_mask.push_back(mask[k]);
+      for (int f = 0; f < 2 * D; ++f) h.rec_cos.push_back(cosf[f]);
+    }
+  }
+  return 0;
+}
+
+double min_spacing(const sem_lbm_mesh* m, int N) {
+  const int D = m->dim, n = N + 1;
+  int NL = 1;
+  for (int a = 0; a < D; ++a) NL *= n;
+  const int stride[3] = {1, n, n * n};
+  double h2 = INFINITY;
+  for (int64_t e = 0; e < m->n_elem; ++e)
+    for (int k = 0; k < NL; ++k)
+      for (int b = 0; b < D; ++b) {
+        const int ib = (b == 0) ? k % n : (b == 1 ? (k / n) % n : k / (n * n));
+        if (ib == N) continue;
+        const double* x0 = m->node_xyz + (e * NL + k) * D;
+        const double* x1 = m->node_xyz + (e * NL + k + stride[b]) * D;
+        double s = 0.0;
+        for (int a = 0; a < D; ++a) s += (x1[a] - x0[a]) * (x1[a] - x0[a]);
+        h2 = std::min(h2, s);
+      }
+  return std::sqrt(h2);
+}
+
+int validate(const sem_lbm_mesh* m, int N, sem_lbm_lattice lat) {
+  if (!m) return fail(SEMLBM_EINVAL, "mesh is NULL");
+  if (m->dim != 2 && m->dim != 3) return fail(SEMLBM_EINVAL, "dim must be 2 or 3");
+  if ((lat == SEMLBM_D2Q9 && m->dim != 2) || (lat == SEMLBM_D3Q13 && m->dim != 3))
+    return fail(SEMLBM_EINVAL, "lattice does not match the mesh dimension");
+  if (lat != SEMLBM_D2Q9 && lat != SEMLBM_D3Q13) return fail(SEMLBM_EUNSUPPORTED, "unknown lattice");
+  const int nmax = (m->dim == 2) ? 16 : 8;
+  if (N < 2 || N > nmax) return fail(SEMLBM_EUNSUPPORTED, "N = %d not built (2..%d)", N, nmax);
+  if (m->n_elem <= 0) return fail(SEMLBM_EINVAL, "n_elem must be positive");
+  if (!m->node_xyz || !m->global_id || !m->face_kind || !m->face_tag)
+    return fail(SEMLBM_EINVAL, "mesh array pointer is NULL");
+  int NL = 1;
+  for (int a = 0; a < m->dim; ++a) NL *= N + 1;
+  if (m->n_elem > (int64_t)(INT32_MAX / 16) / NL) return fail(SEMLBM_EINVAL, "mesh too large");
+  return 0;
+}
+
+// workspace carving
+struct Carve {
+  char* base;
+  size_t off = 0;
+  template <class T>
+  T* take(size_t count) {
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += align_up(count * sizeof(T));
+    return p;
+  }
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+struct sem_lbm {
+  int D, N, n, NL, Q, EPB;
+  sem_lbm_lattice lat;
+  int64_t E, V, G, R;
+  double beta, kappa, tau, theta_w, rho_l, rho_v, dt, mu0f;
+  cudaStream_t stream;
+  bool own_stream = false;
+  void* ws = nullptr;
+  bool own_ws = false;
+  size_t ws_bytes = 0;
+  // device arrays
+  double *f, *fs, *g, *r, *rho, *mu, *lapr, *Fp, *Jinv, *Gm, *Me, *invMg, *xyz, *Dm, *wg;
+  int *off, *idx, *slot, *rec_elem, *rec_node, *rec_mask, *flags;
+  double *wet, *ae, *rec_cos;
+  DiagPart *parts, *dout;
+  int diag_blocks = 0;
+  bool state_ready = false;
+  int64_t step = 0;
+  cudaGraphExec_t graph = nullptr;
+  int kernels_per_step = 0;
+  bool prof_on = false;
+  std::vector<cudaEvent_t> ev;   // event pool; ev[0..nev) recorded since the last read
+  std::vector<int> ev_cls;       // class of the kernel that ends at ev[i] (i >= 1)
+  size_t nev = 0;
+  struct Ops* ops = nullptr;
+};
+
+struct Ops {
+  void (*geom)(sem_lbm&);
+  void (*wall)(sem_lbm&);
+  void (*lap)(sem_lbm&);
+  void (*mu)(sem_lbm&);
+  void (*force)(sem_lbm&);
+  void (*rhs)(sem_lbm&, const double* g);
+  void (*collide)(sem_lbm&);
+  void (*rk)(sem_lbm&, int stage, const double* gcur, double* out);
+  void (*diag)(sem_lbm&);
+  void (*init)(sem_lbm&, const double* rho);
+  void (*density)(sem_lbm&);
+  void (*velocity)(sem_lbm&, double* u);
+  int (*prepare)();
+};
+
+namespace {
+
+constexpr int kDssThreads = 128;
+
+inline int grid_of(int64_t work, int threads) { return (int)((work + threads - 1) / threads); }
+
+template <class L, int NP>
+struct Impl {
+  static constexpr int D = L::D, NL = ipow(NP, D);
+  static constexpr int EPB = (NL >= 256) ? 1 : 256 / NL;
+  static constexpr int NT = EPB * NL;
+  static constexpr int THREADS = ((NT + 31) / 32) * 32;
+  static constexpr size_t SM_LAP = (NP * NP + NT + D * NT) * sizeof(double);
+  static constexpr size_t SM_FORCE = (NP * NP + 2 * NT) * sizeof(double);
+  static constexpr size_t SM_RHS = (NP * NP + 2 * NT + (L::Q - 1) * NT) * sizeof(double);
+  static constexpr size_t SM_GEOM = (NP * NP + D * NT) * sizeof(double);
+
+  static int blocks(const sem_lbm& s) { return (int)((s.E + EPB - 1) / EPB); }
+  static WallDev wall(const sem_lbm& s) { return WallDev{s.slot, s.wet, s.ae, (int)s.R}; }
+
+  static int prepare() {
+    // opt in to large dynamic shared memory where a tile needs it
+    if (SM_RHS > 48 * 1024)
+      if (cudaFuncSetAttribute(k_rhs<L, NP, EPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)SM_RHS) != cudaSuccess)
+        return -1;
+    if (SM_LAP > 48 * 1024)
+      if (cudaFuncSetAttribute(k_lap<L, NP, EPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)SM_LAP) != cudaSuccess)
+        return -1;
+    return 0;
+  }
+  static void geom(sem_lbm& s) {
+    k_geom<D, NP, EPB><<<blocks(s), THREADS, SM_GEOM, s.stream>>>(s.xyz, s.Dm, s.wg, s.Jinv, s.Gm,
+                                                                  s.Me, s.flags, s.V, (int)s.E);
+    k_dss_mass<<<grid_of(s.G, kDssThreads), kDssThreads, 0, s.stream>>>(s.off, s.idx, (int)s.G,
+                                                                        s.Me, s.invMg);
+  }
+  static void wallsetup(sem_lbm& s) {
+    if (s.R == 0) return;
+    k_wall_setup<L, NP><<<grid_of(s.R, 128), 128, 0, s.stream>>>(
+        s.xyz, s.Dm, s.wg, s.rec_elem, s.rec_node, s.rec_cos, s.rec_mask, (int)s.R,
+        std::sqrt(2.0 * s.beta / s.kappa), s.wet, s.ae);
+  }
+  static void lap(sem_lbm& s) {
+    k_lap<L, NP, EPB><<<blocks(s), THREADS, SM_LAP, s.stream>>>(s.rho, s.Gm, wall(s), s.Dm, s.rho_l,
+                                                                s.rho_v, s.lapr, s.V, (int)s.E);
+  }
+  static void mu(sem_lbm& s) {
+    k_dss_mu<<<grid_of(s.G, kDssThreads), kDssThreads, 0, s.stream>>>(
+        s.off, s.idx, (int)s.G, s.lapr, s.rho, s.invMg, s.mu0f * s.beta, s.rho_l, s.rho_v, s.kappa,
+        s.mu);
+  }
+  static void force(sem_lbm& s) {
+    k_force<L, NP, EPB><<<blocks(s), THREADS, SM_FORCE, s.stream>>>(s.rho, s.mu, s.Jinv, s.Me, s.Dm,
+                                                                    s.Fp, s.V, (int)s.E);
+  }
+  static void collide(sem_lbm& s) {
+    k_dss_collide<L><<<grid_of(s.G, kDssThreads), kDssThreads, 0, s.stream>>>(
+        s.off, s.idx, (int)s.G, s.Fp, s.invMg, s.f, s.rho, 1.0 / (s.tau + 0.5), s.dt, s.fs, s.V);
+  }
+  static void rhs(sem_lbm& s, const double* gst) {
+    k_rhs<L, NP, EPB><<<blocks(s), THREADS, SM_RHS, s.stream>>>(gst, s.rho, s.mu, s.Jinv, s.Me,
+                                                                wall(s), s.Dm, s.r, s.V, (int)s.E);
+  }
+  static void rk(sem_lbm& s, int stage, const double* gcur, double* out) {
+    const int gr = grid_of(s.G, kDssThreads);
+    if (stage == 1)
+      k_dss_rk<L, 1><<<gr, kDssThreads, 0, s.stream>>>(s.off, s.idx, (int)s.G, s.r, s.invMg, s.fs,
+                                                       gcur, s.dt, out, s.rho, s.flags + 1, s.V);
+    else if (stage == 2)
+      k_dss_rk<L, 2><<<gr, kDssThreads, 0, s.stream>>>(s.off, s.idx, (int)s.G, s.r, s.invMg, s.fs,
+                                                       gcur, s.dt, out, s.rho, s.flags + 1, s.V);
+    else
+      k_dss_rk<L, 3><<<gr, kDssThreads, 0, s.stream>>>(s.off, s.idx, (int)s.G, s.r, s.invMg, s.fs,
+                                                       gcur, s.dt, out, s.rho, s.flags + 1, s.V);
+  }
+  static void diag(sem_lbm& s) {
+    k_diag<L><<<s.diag_blocks, 256, 0, s.stream>>>(s.f, s.Me, s.parts, s.V);
+    k_diag_final<<<1, 32, 0, s.stream>>>(s.parts, s.diag_blocks, s.dout);
+  }
+  static void init(sem_lbm& s, const double* rho_in) {
+    k_init<L><<<grid_of(s.V, 256), 256, 0, s.stream>>>(rho_in, s.f, s.rho, s.V);
+  }
+  static void density(sem_lbm& s) {
+    k_density<L><<<grid_of(s.V, 256), 256, 0, s.stream>>>(s.f, s.rho, s.V);
+  }
+  static void velocity(sem_lbm& s, double* u) {
+    k_velocity<L><<<grid_of(s.V, 256), 256, 0, s.stream>>>(s.f, u, s.V);
+  }
+  static Ops* ops() {
+    static Ops o{geom, wallsetup, lap, mu, force, rhs, collide, rk, diag, init, density, velocity, prepare};
+    return &o;
+  }
+};
+
+template <class L, int... Ns>
+Ops* pick(int N, std::integer_sequence<int, Ns...>) {
+  Ops* out = nullptr;
+  ((N + 1 == Ns + 3 ? (out = Impl<L, Ns + 3>::ops(), 0) : 0), ...);
+  return out;
+}
+
+Ops* select_ops(sem_lbm_lattice lat, int N) {
+  if (lat == SEMLBM_D2Q9) return pick<D2Q9>(N, std::make_integer_sequence<int, 15>{});  // n = 3..17
+  return pick<D3Q13>(N, std::make_integer_sequence<int, 7>{});                          // n = 3..9
+}
+
+enum { K_LAP = 0, K_MU, K_FORCE, K_COLLIDE, K_RHS, K_RK };
+
+// profiling hook: an event after each launch when per-kernel timing is on
+void mark(sem_lbm& s, int cls);
+
+// one full time step: collision, then three SSP-RK3 stages of streaming
+void enqueue_step(sem_lbm& s) {
+  Ops& o = *s.ops;
+  // rho and mu of fbar^n (rho is current: written by set_density/set_state or the last stage)
+  o.lap(s); mark(s, K_LAP);
+  o.mu(s); mark(s, K_MU);
+  o.force(s); mark(s, K_FORCE);
+  o.collide(s); mark(s, K_COLLIDE);          // fs = f* (RK base state U0)
+  o.rhs(s, s.fs); mark(s, K_RHS);            // stage 1 reuses rho, mu of fbar^n
+  o.rk(s, 1, s.fs, s.g); mark(s, K_RK);
+  for (int stage = 2; stage <= 3; ++stage) {
+    o.lap(s); mark(s, K_LAP);
+    o.mu(s); mark(s, K_MU);
+    o.rhs(s, s.g); mark(s, K_RHS);
+    o.rk(s, stage, s.g, stage == 3 ? s.f : s.g); mark(s, K_RK);
+  }
+}
+
+int count_kernels_per_step() { return 6 + 2 * 4; }
+
+bool record_event(sem_lbm& s, int cls) {
+  if (s.nev == s.ev.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return false;
+    s.ev.push_back(e);
+    s.ev_cls.push_back(-1);
+  }
+  s.ev_cls[s.nev] = cls;
+  if (cudaEventRecord(s.ev[s.nev], s.stream) != cudaSuccess) return false;
+  ++s.nev;
+  return true;
+}
+
+void mark(sem_lbm& s, int cls) {
+  if (s.prof_on) record_event(s, cls);
+}
+
+size_t layout(sem_lbm& s, char* base) {
+  Carve c{base};
+  const int64_t V = s.V, Q = s.Q, D = s.D;
+  s.f = c.take<double>(Q * V);
+  s.fs = c.take<double>(Q * V);
+  s.g = c.take<double>(Q * V);
+  s.r = c.take<double>(Q * V);
+  s.rho = c.take<double>(V);
+  s.mu = c.take<double>(V);
+  s.lapr = c.take<double>(V);
+  s.Fp = c.take<double>(D * V);
+  s.Jinv = c.take<double>(D * D * V);
+  s.Gm = c.take<double>(D * (D + 1) / 2 * V);
+  s.Me = c.take<double>(V);
+  s.invMg = c.take<double>(s.G);
+  s.xyz = c.take<double>(D * V);
+  s.Dm = c.take<double>(s.n * s.n);
+  s.wg = c.take<double>(s.n);
+  s.off = c.take<int>(s.G + 1);
+  s.idx = c.take<int>(V);
+  s.slot = c.take<int>(V);
+  const int64_t R = std::max<int64_t>(s.R, 1);
+  s.wet = c.take<double>(R);
+  s.ae = c.take<double>(Q * R);
+  s.rec_elem = c.take<int>(R);
+  s.rec_node = c.take<int>(R);
+  s.rec_mask = c.take<int>(R);
+  s.rec_cos = c.take<double>(R * 2 * D);
+  s.flags = c.take<int>(8);
+  s.parts = c.take<DiagPart>(s.diag_blocks);
+  s.dout = c.take<DiagPart>(1);
+  return c.off;
+}
+
+int diag_blocks_for(int64_t V) { return (int)std::min<int64_t>(1184, (V + 255) / 256); }
+
+int host_copy_in(sem_lbm* s, void* dst, const void* src, size_t bytes, int src_on_device) {
+  CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, src_on_device ? cudaMemcpyDeviceToDevice
+                                                         : cudaMemcpyHostToDevice, s->stream));
+  if (!src_on_device) CUDA_TRY(cudaStreamSynchronize(s->stream));
+  return 0;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+const char* sem_lbm_last_error(void) { return g_err.c_str(); }
+
+size_t sem_lbm_workspace_bytes(const sem_lbm_mesh* mesh, int N, sem_lbm_lattice lattice) {
+  if (validate(mesh, N, lattice)) return 0;
+  HostMaps h;
+  sem_lbm_params p{};
+  std::vector<double> many(64, M_PI / 2);
+  p.n_tags = 64;
+  p.theta_tag = many.data();
+  if (build_maps(mesh, N, M_PI / 2, &p, h)) return 0;
+  sem_lbm s{};
+  s.D = mesh->dim;
+  s.N = N;
+  s.n = N + 1;
+  s.NL = ipow(s.n, s.D);
+  s.Q = (lattice == SEMLBM_D2Q9) ? 9 : 13;
+  s.E = mesh->n_elem;
+  s.V = s.E * s.NL;
+  s.G = h.G;
+  s.R = (int64_t)h.rec_elem.size();
+  s.diag_blocks = diag_blocks_for(s.V);
+  return layout(s, nullptr);
+}
+
+int sem_lbm_create(const sem_lbm_mesh* mesh, int N, sem_lbm_lattice lattice, double beta,
+                   double kappa, double tau, double theta_w, const sem_lbm_params* params,
+                   sem_lbm_t** out) {
+  g_err.clear();
+  if (!out) return fail(SEMLBM_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (int rc = validate(mesh, N, lattice)) return rc;
+  if (!(beta > 0) || !(kappa > 0) || !(tau > 0) || !std::isfinite(theta_w))
+    return fail(SEMLBM_EINVAL, "beta, kappa, tau must be positive and theta_w finite");
+  sem_lbm_params p{};
+  if (params) p = *params;
+  HostMaps h;
+  if (int rc = build_maps(mesh, N, theta_w, &p, h)) return rc;
+
+  sem_lbm* s = new (std::nothrow) sem_lbm();
+  if (!s) return fail(SEMLBM_ENOMEM, "host allocation failed");
+  s->lat = lattice;
+  s->D = mesh->dim;
+  s->N = N;
+  s->n = N + 1;
+  s->NL = ipow(s->n, s->D);
+  s->Q = (lattice == SEMLBM_D2Q9) ? 9 : 13;
+  s->E = mesh->n_elem;
+  s->V = s->E * s->NL;
+  s->G = h.G;
+  s->R = (int64_t)h.rec_elem.size();
+  s->beta = beta;
+  s->kappa = kappa;
+  s->tau = tau;
+  s->theta_w = theta_w;
+  s->rho_l = p.rho_l > 0 ? p.rho_l : 1.0;
+  s->rho_v = p.rho_v > 0 ? p.rho_v : 0.1;
+  s->mu0f = p.mu0_factor > 0 ? p.mu0_factor : 2.0;
+  const double speed = (lattice == SEMLBM_D2Q9) ? D2Q9::SPEED_MAX : D3Q13::SPEED_MAX;
+  if (p.dt > 0) {
+    s->dt = p.dt;
+  } else {
+    // advective CFL on the smallest GLL spacing, and the capillary-wave bound
+    // dt <= 0.1 h^2 / sqrt(rho_l kappa) (omega ~ sqrt(rho kappa) k^2)
+    const double h = min_spacing(mesh, N);
+    s->dt = std::min((p.cfl > 0 ? p.cfl : 0.4) * h / speed, 0.1 * h * h / std::sqrt(s->rho_l * kappa));
+  }
+  s->diag_blocks = diag_blocks_for(s->V);
+  s->ops = select_ops(lattice, N);
+  s->kernels_per_step = count_kernels_per_step();
+  auto bail = [&](int rc) {
+    sem_lbm_destroy(s);
+    return rc;
+  };
+  if (!s->ops) return bail(fail(SEMLBM_EUNSUPPORTED, "no kernels for N = %d", N));
+  if (s->ops->prepare() != 0) return bail(fail(SEMLBM_ECUDA, "cudaFuncSetAttribute failed"));
+
+  if (p.stream) {
+    s->stream = (cudaStream_t)p.stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess)
+      return bail(fail(SEMLBM_ECUDA, "cudaStreamCreate failed"));
+    s->own_stream = true;
+  }
+  s->ws_bytes = layout(*s, nullptr);
+  if (p.workspace) {
+    if (p.workspace_bytes < s->ws_bytes)
+      return bail(fail(SEMLBM_ENOMEM, "workspace of %zu bytes is below the %zu needed",
+                       p.workspace_bytes, s->ws_bytes));
+    if (((uintptr_t)p.workspace) & 255) return bail(fail(SEMLBM_EINVAL, "workspace must be 256-byte aligned"));
+    s->ws = p.workspace;
+  } else {
+    if (cudaMalloc(&s->ws, s->ws_bytes) != cudaSuccess) {
+      s->ws = nullptr;
+      return bail(fail(SEMLBM_ENOMEM, "cudaMalloc of %zu bytes failed", s->ws_bytes));
+    }
+    s->own_ws = true;
+  }
+  layout(*s, (char*)s->ws);
+
+  std::vector<double> x, w, Dm;
+  gll_tables(N, x, w, Dm);
+  const int D = s->D;
+  cudaStream_t st = s->stream;
+  auto up = [&](void* dst, const void* src, size_t bytes) {
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st) == cudaSuccess;
+  };
+  bool ok = up(s->xyz, mesh->node_xyz, sizeof(double) * D * s->V) &&
+            up(s->Dm, Dm.data(), sizeof(double) * s->n * s->n) &&
+            up(s->wg, w.data(), sizeof(double) * s->n) &&
+            up(s->off, h.off.data(), sizeof(int) * (s->G + 1)) &&
+            up(s->idx, h.idx.data(), sizeof(int) * s->V) &&
+            up(s->slot, h.slot.data(), sizeof(int) * s->V) &&
+            cudaMemsetAsync(s->flags, 0, 8 * sizeof(int), st) == cudaSuccess;
+  if (ok && s->R > 0)
+    ok = up(s->rec_elem, h.rec_elem.data(), sizeof(int) * s->R) &&
+         up(s->rec_node, h.rec_node.data(), sizeof(int) * s->R) &&
+         up(s->rec_mask, h.rec_mask.data(), sizeof(int) * s->R) &&
+         up(s->rec_cos, h.rec_cos.data(), sizeof(double) * s->R * 2 * D);
+  if (!ok) return bail(fail(SEMLBM_ECUDA, "upload failed: %s", cudaGetErrorString(cudaGetLastError())));
+  s->ops->geom(*s);
+  s->ops->wall(*s);
+  int flags[2] = {0, 0};
+  if (cudaMemcpyAsync(flags, s->flags, sizeof flags, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return bail(fail(SEMLBM_ECUDA, "geometry setup failed: %s", cudaGetErrorString(cudaGetLastError())));
+  if (flags[0]) return bail(fail(SEMLBM_EINVAL, "mesh has an element with non-positive Jacobian"));
+  *out = s;
+  return SEMLBM_OK;
+}
+
+int sem_lbm_set_density(sem_lbm_t* s, const double* rho, int on_device) {
+  if (!s || !rho) return fail(SEMLBM_EINVAL, "NULL argument");
+  double* src = s->lapr;   // staging for host data (overwritten by the next step anyway)
+  if (int rc = host_copy_in(s, src, rho, sizeof(double) * s->V, on_device)) return rc;
+  CUDA_TRY(cudaMemsetAsync(s->flags, 0, 8 * sizeof(int), s->stream));
+  s->ops->init(*s, src);
+  CUDA_TRY(cudaGetLastError());
+  s->state_ready = true;
+  s->step = 0;
+  return 0;
+}
+
+int sem_lbm_set_state(sem_lbm_t* s, const double* fbar, int on_device, int64_t step) {
+  if (!s || !fbar) return fail(SEMLBM_EINVAL, "NULL argument");
+  if (int rc = host_copy_in(s, s->f, fbar, sizeof(double) * s->Q * s->V, on_device)) return rc;
+  s->ops->density(*s);
+  CUDA_TRY(cudaGetLastError());
+  s->state_ready = true;
+  s->step = step;
+  return 0;
+}
+
+int sem_lbm_step(sem_lbm_t* s, int64_t n_steps) {
+  if (!s) return fail(SEMLBM_EINVAL, "NULL solver");
+  if (n_steps < 0) return fail(SEMLBM_EINVAL, "n_steps must be >= 0");
+  if (!s->state_ready) return fail(SEMLBM_EINVAL, "state not set (call sem_lbm_set_density)");
+  if (n_steps == 0) return 0;
+  if (s->prof_on) {
+    if (s->nev == 0 && !record_event(*s, -1)) return fail(SEMLBM_ECUDA, "cudaEventRecord failed");
+    for (int64_t i = 0; i < n_steps; ++i) enqueue_step(*s);
+    CUDA_TRY(cudaGetLastError());
+    s->step += n_steps;
+    return 0;
+  }
+  if (!s->graph) {
+    cudaGraph_t gr;
+    CUDA_TRY(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
+    enqueue_step(*s);
+    cudaError_t e1 = cudaStreamEndCapture(s->stream, &gr);
+    if (e1 != cudaSuccess) return fail(SEMLBM_ECUDA, "graph capture: %s", cudaGetErrorString(e1));
+    cudaError_t e2 = cudaGraphInstantiate(&s->graph, gr, 0);
+    cudaGraphDestroy(gr);
+    if (e2 != cudaSuccess) {
+      s->graph = nullptr;
+      return fail(SEMLBM_ECUDA, "graph instantiate: %s", cudaGetErrorString(e2));
+    }
+  }
+  for (int64_t i = 0; i < n_steps; ++i) CUDA_TRY(cudaGraphLaunch(s->graph, s->stream));
+  s->step += n_steps;
+  return 0;
+}
+
+int sem_lbm_diagnostics(sem_lbm_t* s, sem_lbm_diag* out) {
+  if (!s || !out) return fail(SEMLBM_EINVAL, "NULL argument");
+  if (!s->state_ready) return fail(SEMLBM_EINVAL, "state not set");
+  s->ops->diag(*s);
+  CUDA_TRY(cudaGetLastError());
+  DiagPart d;
+  int flags[2];
+  CUDA_TRY(cudaMemcpyAsync(&d, s->dout, sizeof d, cudaMemcpyDeviceToHost, s->stream));
+  CUDA_TRY(cudaMemcpyAsync(flags, s->flags, sizeof flags, cudaMemcpyDeviceToHost, s->stream));
+  CUDA_TRY(cudaStreamSynchronize(s->stream));
+  out->step = s->step;
+  out->time = s->step * s->dt;
+  out->mass = d.mass;
+  out->ke_max = d.ke_max;
+  out->ke_int = d.ke_int;
+  out->umax = std::sqrt(d.u2max);
+  out->rho_min = d.rho_min;
+  out->rho_max = d.rho_max;
+  out->n_nonfinite = (int64_t)d.nonfinite;
+  out->status = (d.nonfinite > 0 || flags[1]) ? SEMLBM_ENONFINITE : SEMLBM_OK;
+  return 0;
+}
+
+int sem_lbm_get_field(sem_lbm_t* s, int which, double* dst, int dst_on_device) {
+  if (!s || !dst) return fail(SEMLBM_EINVAL, "NULL argument");
+  if (!s->state_ready) return fail(SEMLBM_EINVAL, "state not set");
+  const double* src;
+  size_t count;
+  switch (which) {
+    case 0: src = s->f; count = (size_t)s->Q * s->V; break;
+    case 1: src = s->rho; count = s->V; break;
+    case 2: s->ops->velocity(*s, s->Fp); src = s->Fp; count = (size_t)s->D * s->V; break;
+    case 3: s->ops->lap(*s); s->ops->mu(*s); src = s->mu; count = s->V; break;
+    default: return fail(SEMLBM_EINVAL, "unknown field %d", which);
+  }
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaMemcpyAsync(dst, src, count * sizeof(double),
+                           dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                           s->stream));
+  if (!dst_on_device) CUDA_TRY(cudaStreamSynchronize(s->stream));
+  return 0;
+}
+
+int sem_lbm_get_state(sem_lbm_t* s, double* fbar, int on_device, int64_t* step) {
+  if (int rc = sem_lbm_get_field(s, 0, fbar, on_device)) return rc;
+  if (step) *step = s->step;
+  return 0;
+}
+
+int sem_lbm_get_info(const sem_lbm_t* s, sem_lbm_info_t* out) {
+  if (!s || !out) return fail(SEMLBM_EINVAL, "NULL argument");
+  out->dim = s->D;
+  out->N = s->N;
+  out->Q = s->Q;
+  out->n_elem = s->E;
+  out->n_local = s->V;
+  out->n_global = s->G;
+  out->n_wall_nodes = s->R;
+  out->dt = s->dt;
+  out->kappa = s->kappa;
+  out->beta = s->beta;
+  out->tau = s->tau;
+  out->workspace_bytes = s->ws_bytes;
+  out->graph_launches = 1;
+  out->kernels_per_step = s->kernels_per_step;
+  return 0;
+}
+
+int sem_lbm_profile(sem_lbm_t* s, int enable) {
+  if (!s) return fail(SEMLBM_EINVAL, "NULL solver");
+  s->prof_on = enable != 0;
+  s->nev = 0;
+  return 0;
+}
+
+int sem_lbm_profile_read(sem_lbm_t* s, sem_lbm_profile_t* out) {
+  if (!s || !out) return fail(SEMLBM_EINVAL, "NULL argument");
+  memset(out, 0, sizeof *out);
+  CUDA_TRY(cudaStreamSynchronize(s->stream));
+  for (size_t i = 1; i < s->nev; ++i) {
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, s->ev[i - 1], s->ev[i]));
+    const int c = s->ev_cls[i];
+    if (c >= 0 && c < 8) {
+      out->ms[c] += ms;
+      out->launches[c] += 1;
+    }
+  }
+  if (s->nev > 1) {
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, s->ev[0], s->ev[s->nev - 1]));
+    out->total_ms = ms;
+  }
+  s->nev = 0;
+  return 0;
+}
+
+void sem_lbm_destroy(sem_lbm_t* s) {
+  if (!s) return;
+  if (s->stream) cudaStreamSynchronize(s->stream);
+  for (cudaEvent_t e : s->ev) cudaEventDestroy(e);
+  if (s->graph) cudaGraphExecDestroy(s->graph);
+  if (s->own_ws && s->ws) cudaFree(s->ws);
+  if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+  delete s;
+}
+
+}  // extern "C"

@@ -304,12 +304,25 @@ def kappa_from_width(beta, delta, rho_l, rho_v):
     return beta * delta ** 2 * (rho_l - rho_v) ** 2 / 8
 
 
-def cfl_dt(mesh, lattice, cfl=0.5):
-    return cfl * min_node_spacing(mesh) / SPEED_MAX[lattice]
+CAPILLARY_NUMBER = 0.1
+
+
+def cfl_dt(mesh, lattice, cfl=0.4, kappa=None, rho_l=1.0):
+    """Time step: min(cfl h_min / max|e|, 0.1 h_min^2 / sqrt(rho_l kappa)).
+
+    The second bound keeps the fastest capillary wave (omega ~ sqrt(rho kappa) k^2,
+    from the kappa lap(rho) part of mu in the streaming force) inside the SSP-RK3
+    stability region; the library applies the same rule when given dt <= 0.
+    """
+    h = min_node_spacing(mesh)
+    dt = cfl * h / SPEED_MAX[lattice]
+    if kappa:
+        dt = min(dt, CAPILLARY_NUMBER * h * h / math.sqrt(rho_l * kappa))
+    return dt
 
 
 def flat_wall_2d(N=4, ne=(8, 8), theta=math.radians(60), R=0.25, beta=1e-3, tau=0.5,
-                 width_spacings=4.0, rho_l=1.0, rho_v=0.1, steps=200, cfl=0.5, seed=None,
+                 width_spacings=4.0, rho_l=1.0, rho_v=0.1, steps=200, cfl=0.4, seed=None,
                  noise=0.0):
     """Sessile half-disc on the wall y = 0 of the unit square (Sec. 3.1 shape)."""
     mesh = box(ne, (0.0, 0.0), (1.0, 1.0), N, face_tags={2: 0})
@@ -318,12 +331,13 @@ def flat_wall_2d(N=4, ne=(8, 8), theta=math.radians(60), R=0.25, beta=1e-3, tau=
     rho0 = droplet_density(mesh, (0.5, 0.0), R, delta, rho_l, rho_v)
     if noise:
         rho0 = rho0 + node_noise(mesh, seed or 0, noise)
-    return Case("flat2d", mesh, "D2Q9", rho_l, rho_v, beta, kappa, tau, cfl_dt(mesh, "D2Q9", cfl),
+    return Case("flat2d", mesh, "D2Q9", rho_l, rho_v, beta, kappa, tau,
+                cfl_dt(mesh, "D2Q9", cfl, kappa, rho_l),
                 theta, (), rho0, steps, {"delta": delta})
 
 
 def cylinder_2d(theta=math.radians(90), N=6, n_theta=64, n_r=16, Rc=0.1, beta=1e-2, tau=0.5,
-                rho_l=1.0, rho_v=0.1, noise=1e-3, seed=1, perm_seed=2, cfl=0.5, steps=200):
+                rho_l=1.0, rho_v=0.1, noise=1e-3, seed=1, perm_seed=2, cfl=0.4, steps=200):
     """Droplet of radius 0.3 Rc touching a cylinder (Sec. 3.2 shape), curved O-grid."""
     mesh = rotate_elements(cylinder_ogrid(N, n_theta, n_r, Rc), perm_seed)
     Rd = 0.3 * Rc
@@ -333,16 +347,16 @@ def cylinder_2d(theta=math.radians(90), N=6, n_theta=64, n_r=16, Rc=0.1, beta=1e
     rho0 = droplet_density(mesh, (0.5, 0.5 + Rc + Rd), Rd, delta, rho_l, rho_v)
     rho0 = rho0 + node_noise(mesh, seed, noise)
     return Case("cylinder2d", mesh, "D2Q9", rho_l, rho_v, beta, kappa, tau,
-                cfl_dt(mesh, "D2Q9", cfl), theta, (), rho0, steps, {"delta": delta})
+                cfl_dt(mesh, "D2Q9", cfl, kappa, rho_l), theta, (), rho0, steps, {"delta": delta})
 
 
 def sphere_3d(N=5, ne=(16, 16, 16), theta=math.radians(60), beta=1e-3, Cn=0.08, d=0.25,
-              La=60.0, rho_l=1.0, rho_v=0.1, cfl=0.5, steps=20000):
+              La=60.0, rho_l=1.0, rho_v=0.1, cfl=0.4, steps=20000):
     """3D droplet (d = 0.25 at (0.25, 0.25, 0.04)) on a sphere-cap bottom (Sec. 3.2)."""
     mesh = sphere_cap_box(N, ne)
     delta = Cn * d
     kappa = kappa_from_width(beta, delta, rho_l, rho_v)
-    dt = cfl_dt(mesh, "D3Q13", cfl)
+    dt = cfl_dt(mesh, "D3Q13", cfl, kappa, rho_l)
     gamma = (rho_l - rho_v) ** 3 * math.sqrt(2 * kappa * beta) / 6
     eta = math.sqrt(gamma * d / La)          # La = gamma d / eta^2
     nu = eta / rho_l
@@ -353,7 +367,7 @@ def sphere_3d(N=5, ne=(16, 16, 16), theta=math.radians(60), beta=1e-3, Cn=0.08, 
 
 
 def periodic_droplet(dim=2, ne=4, N=8, L=1.0, D=0.5, Cn=0.063, beta=1e-3, tau=0.5,
-                     rho_l=1.0, rho_v=0.1, cfl=0.5, steps=200):
+                     rho_l=1.0, rho_v=0.1, cfl=0.4, steps=200):
     """Isolated droplet in a periodic box (Sec. 3.3)."""
     mesh = box((ne,) * dim, (0.0,) * dim, (L,) * dim, N, periodic=(True,) * dim)
     delta = Cn * D
@@ -361,4 +375,4 @@ def periodic_droplet(dim=2, ne=4, N=8, L=1.0, D=0.5, Cn=0.063, beta=1e-3, tau=0.
     lat = "D2Q9" if dim == 2 else "D3Q13"
     rho0 = droplet_density(mesh, (L / 2,) * dim, D / 2, delta, rho_l, rho_v)
     return Case("droplet%dd" % dim, mesh, lat, rho_l, rho_v, beta, kappa, tau,
-                cfl_dt(mesh, lat, cfl), math.pi / 2, (), rho0, steps, {"delta": delta})
+                cfl_dt(mesh, lat, cfl, kappa, rho_l), math.pi / 2, (), rho0, steps, {"delta": delta})

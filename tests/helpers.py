@@ -20,3 +20,13 @@ def oracle_of(case, **over):
 
 def local_shape(case):
     return (case.mesh.n_elem,) + (case.mesh.N + 1,) * case.mesh.dim
+
+
+def make_case(name, mesh, lattice, beta, delta, tau, theta_w, theta_tag=(), rho0=None,
+              rho_l=1.0, rho_v=0.1, cfl=0.4):
+    """A Case with kappa from the interface width and the stable default dt."""
+    from paper_2609_00535_b300 import inputs
+    kappa = inputs.kappa_from_width(beta, delta, rho_l, rho_v)
+    dt = inputs.cfl_dt(mesh, lattice, cfl, kappa, rho_l)
+    return inputs.Case(name, mesh, lattice, rho_l, rho_v, beta, kappa, tau, dt, theta_w,
+                       tuple(theta_tag), rho0)

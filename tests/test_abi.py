@@ -1,0 +1,74 @@
+"""CPU checks of the C ABI: the library loads, exports every declared entry
+point, and rejects invalid input on the host before touching a GPU."""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2609_00535_b300 import inputs, semlbm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(sem_lbm_\w+)\s*\(", txt))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = semlbm.load()
+    names = declared_symbols()
+    assert {"sem_lbm_create", "sem_lbm_step", "sem_lbm_diagnostics"} <= names
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(semlbm.EXPORTED) <= names
+
+
+def _create(mesh, N, lattice, theta_tag=(), beta=1e-3, kappa=1e-6, tau=0.5):
+    lib = semlbm.load()
+    m, keep = semlbm.mesh_struct(mesh)
+    tags = np.asarray(theta_tag, dtype=np.float64)
+    p = semlbm.ParamsC(1.0, 0.1, 0.01, 0.0, 0.0, len(tags), tags.ctypes.data if len(tags) else None,
+                       None, None, 0)
+    h = ctypes.c_void_p()
+    rc = lib.sem_lbm_create(ctypes.byref(m), N, lattice, beta, kappa, tau, math.pi / 3,
+                            ctypes.byref(p), ctypes.byref(h))
+    return rc, lib.sem_lbm_last_error().decode()
+
+
+def test_host_validation_errors():
+    m2 = inputs.box((2, 2), (0, 0), (1, 1), 4, face_tags={2: 0})
+    m3 = inputs.box((1, 1, 1), (0, 0, 0), (1, 1, 1), 3)
+    rc, msg = _create(m2, 4, semlbm.D3Q13)
+    assert rc == -1 and "lattice" in msg
+    rc, msg = _create(m2, 17, semlbm.D2Q9)
+    assert rc == -6
+    rc, msg = _create(m3, 9, semlbm.D3Q13)
+    assert rc == -6
+    rc, msg = _create(m2, 4, semlbm.D2Q9, beta=-1.0)
+    assert rc == -1
+    bad = inputs.box((2, 2), (0, 0), (1, 1), 4, face_tags={2: 3})   # tag 3 has no angle
+    rc, msg = _create(bad, 4, semlbm.D2Q9, theta_tag=(1.0,))
+    assert rc == -1 and "tag 3" in msg
+    fk = inputs.box((2, 2), (0, 0), (1, 1), 4)
+    fk.face_kind[0, 0] = 7
+    rc, msg = _create(fk, 4, semlbm.D2Q9)
+    assert rc == -1 and "face_kind" in msg
+
+
+def test_workspace_bytes_is_host_only_and_scales():
+    b1 = semlbm.workspace_bytes(inputs.box((2, 2), (0, 0), (1, 1), 4), 4, "D2Q9")
+    b2 = semlbm.workspace_bytes(inputs.box((4, 4), (0, 0), (1, 1), 4), 4, "D2Q9")
+    assert 0 < b1 < b2
+    # 4 state copies of Q*V doubles dominate
+    V = 16 * 25
+    assert b2 > 4 * 9 * V * 8
+    assert semlbm.workspace_bytes(inputs.box((2, 2), (0, 0), (1, 1), 4), 4, "D3Q13") == 0

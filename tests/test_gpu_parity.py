@@ -1,0 +1,173 @@
+"""GPU (C ABI) against the oracle, element by element, on the same seeded inputs.
+
+Tolerance: max |x_gpu - x_oracle| / max |x_oracle| <= 1e-12 for fbar and rho
+(the FP64 step differs from the oracle only in summation order and FMA
+contraction; the measured drift is ~1e-15 per step), after the stated number of
+steps.  Sizes span several CTA tiles and a ragged last tile.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2609_00535_b300 import inputs
+from tests.helpers import make_case, oracle_of
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+
+
+def _solver(case):
+    from paper_2609_00535_b300 import semlbm
+    s = semlbm.Solver.from_case(case)
+    s.set_density(case.rho0)
+    return s
+
+
+def _oracle_run(case, steps):
+    om, orc = oracle_of(case)
+    f = orc.initial_state(case.rho0.reshape(om.shape))
+    return om, orc, orc.run(f, steps)
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+def _compare(case, steps, tol=TOL):
+    s = _solver(case)
+    s.step(steps)
+    f_gpu, step = s.get_state()
+    assert step == steps
+    om, orc, f_ref = _oracle_run(case, steps)
+    f_ref = f_ref.reshape(f_gpu.shape)
+    err = _rel(f_gpu, f_ref)
+    rho_gpu = s.field("rho")
+    rho_ref = f_ref.sum(0)
+    assert err <= tol, err
+    assert _rel(rho_gpu, rho_ref) <= tol
+    d = s.diagnostics()
+    dref = orc.diagnostics(f_ref.reshape((f_ref.shape[0],) + om.shape))
+    assert d["status"] == 0
+    assert abs(d["mass"] - dref["mass"]) <= 1e-13 * dref["mass"]
+    assert abs(d["ke_max"] - dref["ke_max"]) <= 1e-9 * max(dref["ke_max"], 1e-300) + 1e-30
+    s.close()
+    return err
+
+
+def test_flat_wall_1000_steps():
+    """2D D2Q9 sessile droplet, 8x8 quads, N = 4 (1,600 nodes), 60 degrees."""
+    _compare(inputs.flat_wall_2d(), 1000)
+
+
+def test_curved_rotated_cylinder_mesh():
+    mesh = inputs.rotate_elements(inputs.cylinder_ogrid(6, n_theta=16, n_r=3), 2)
+    case = make_case("cyl", mesh, "D2Q9", 1e-2, 0.04, 0.5, math.radians(30),
+                     rho0=inputs.droplet_density(mesh, (0.5, 0.63), 0.04, 0.04)
+                     + inputs.node_noise(mesh, 1, 1e-3))
+    _compare(case, 300)
+
+
+def test_sphere_3d_small():
+    case = inputs.sphere_3d(N=4, ne=(3, 3, 2), Cn=0.3)
+    _compare(case, 100)
+
+
+@pytest.mark.parametrize("dim,N,ne", [(2, 8, 4), (3, 4, 2)])
+def test_periodic_droplet(dim, N, ne):
+    case = inputs.periodic_droplet(dim=dim, ne=ne, N=N, Cn=0.25)
+    _compare(case, 100 if dim == 2 else 40)
+
+
+@pytest.mark.parametrize("N", [2, 3, 5, 7, 11, 16])
+def test_orders_2d_ragged_tiles(N):
+    """Element counts that leave the last CTA tile partly empty."""
+    mesh = inputs.rotate_elements(inputs.box((3, 5), (0, 0), (1.0, 1.2), N, face_tags={2: 0, 0: 1}), N)
+    case = make_case("o2", mesh, "D2Q9", 1e-2, 0.2, 0.6, math.radians(50), (math.radians(120),),
+                     rho0=inputs.droplet_density(mesh, (0.4, 0.1), 0.3, 0.2))
+    _compare(case, 20)
+
+
+@pytest.mark.parametrize("N", [2, 3, 5, 6, 8])
+def test_orders_3d(N):
+    mesh = inputs.rotate_elements(inputs.box((3, 1, 2), (0, 0, 0), (1.0, 0.5, 0.7), N,
+                                             face_tags={4: 0, 1: 1}), N)
+    case = make_case("o3", mesh, "D3Q13", 1e-2, 0.3, 0.6, math.radians(70), (math.radians(110),),
+                     rho0=inputs.droplet_density(mesh, (0.4, 0.2, 0.1), 0.3, 0.3))
+    _compare(case, 10)
+
+
+def test_single_element():
+    mesh = inputs.box((1, 1), (0, 0), (1, 1), 6, face_tags={2: 0})
+    case = make_case("one", mesh, "D2Q9", 1e-2, 0.3, 0.5, math.radians(60),
+                     rho0=inputs.droplet_density(mesh, (0.5, 0.0), 0.35, 0.3))
+    _compare(case, 30)
+
+
+def test_chemical_potential_and_velocity_fields():
+    case = inputs.flat_wall_2d(N=5, ne=(3, 4), noise=1e-3, seed=4)
+    s = _solver(case)
+    s.step(7)
+    om, orc, f_ref = _oracle_run(case, 7)
+    rho = orc.density(f_ref)
+    mu_ref = orc.chemical_potential(rho).reshape(-1)
+    u_ref = orc.velocity(f_ref, rho).reshape(-1, 2).T
+    assert _rel(s.field("mu"), mu_ref) <= 1e-11
+    assert np.abs(s.field("u") - u_ref).max() <= 1e-12 * max(np.abs(u_ref).max(), 1e-6)
+    s.close()
+
+
+def test_checkpoint_restart_is_bitwise():
+    case = inputs.flat_wall_2d(N=4, ne=(4, 4))
+    a = _solver(case)
+    a.step(30)
+    st, k = a.get_state()
+    a.step(20)
+    fa, _ = a.get_state()
+    b = _solver(case)
+    b.set_state(st, k)
+    b.step(20)
+    fb, kb = b.get_state()
+    assert kb == 50 and np.array_equal(fa, fb)
+    # one call of n steps equals n calls of one step
+    c = _solver(case)
+    for _ in range(50):
+        c.step(1)
+    assert np.array_equal(c.get_state()[0], fa)
+    a.close(); b.close(); c.close()
+
+
+def test_uniform_state_stationary_on_gpu():
+    case = inputs.flat_wall_2d(N=4, ne=(4, 4), theta=math.radians(30))
+    case.rho0 = np.full_like(case.rho0, 1.0)
+    s = _solver(case)
+    f0, _ = s.get_state()
+    s.step(500)
+    f1, _ = s.get_state()
+    assert np.abs(f1 - f0).max() <= 1e-15
+    s.close()
+
+
+def test_mass_conservation_gpu_curved_2000_steps():
+    mesh = inputs.rotate_elements(inputs.cylinder_ogrid(6, n_theta=32, n_r=8), 2)
+    case = make_case("cylm", mesh, "D2Q9", 1e-2, 0.03, 0.5, math.radians(45),
+                     rho0=inputs.droplet_density(mesh, (0.5, 0.64), 0.05, 0.03))
+    s = _solver(case)
+    m0 = s.diagnostics()["mass"]
+    s.step(2000)
+    d = s.diagnostics()
+    assert d["status"] == 0 and abs(d["mass"] - m0) <= 1e-12 * m0
+    s.close()
+
+
+def test_default_time_step_rule():
+    """dt <= 0 in create -> min(0.4 h_min/max|e|, 0.1 h_min^2/sqrt(rho_l kappa))."""
+    from paper_2609_00535_b300 import semlbm
+    for case in (inputs.flat_wall_2d(), inputs.sphere_3d(N=4, ne=(2, 2, 2)),
+                 make_case("cap", inputs.box((2, 2), (0, 0), (1, 1), 12), "D2Q9", 1e-1, 0.3, 0.5,
+                           math.pi / 2)):
+        s = semlbm.Solver(case.mesh, case.lattice, case.beta, case.kappa, case.tau, case.theta_w,
+                          dt=0.0)
+        assert abs(s.info["dt"] - case.dt) <= 1e-12 * case.dt, (s.info["dt"], case.dt)
+        s.close()

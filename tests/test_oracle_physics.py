@@ -16,7 +16,7 @@ import pytest
 
 from paper_2609_00535_b300 import inputs
 from oracle import lattice, method
-from tests.helpers import oracle_mesh, oracle_of, local_shape
+from tests.helpers import make_case, oracle_mesh, oracle_of, local_shape
 
 
 def _solver(mesh, **kw):
@@ -110,8 +110,7 @@ def test_mass_conserved_flat_wall_1000_steps():
 
 def test_mass_conserved_curved_rotated_walls():
     mesh = inputs.rotate_elements(inputs.cylinder_ogrid(5, n_theta=8, n_r=3), 9)
-    c = inputs.Case("cyl", mesh, "D2Q9", 1.0, 0.1, 1e-2, inputs.kappa_from_width(1e-2, 0.05, 1, .1),
-                    0.5, inputs.cfl_dt(mesh, "D2Q9"), math.radians(40))
+    c = make_case("cyl", mesh, "D2Q9", 1e-2, 0.05, 0.5, math.radians(40))
     om, s = oracle_of(c)
     rho = inputs.droplet_density(mesh, (0.5, 0.63), 0.05, 0.05) + inputs.node_noise(mesh, 1, 1e-3)
     f = s.initial_state(rho.reshape(om.shape))
