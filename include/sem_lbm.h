@@ -172,6 +172,33 @@ typedef struct {
 int sem_lbm_profile(sem_lbm_t* s, int enable);
 int sem_lbm_profile_read(sem_lbm_t* s, sem_lbm_profile_t* out);
 
+/* Allocation-free chemical potential.  Computes mu = mu0(rho) - kappa lap(rho)
+ * for a caller-supplied density field on this solver's mesh, like
+ * sem_lbm_get_field(s, 3, ...), but without using any device memory beyond
+ * what already exists: the element-local Laplacian partials (the one piece of
+ * scratch this computation needs) live in a fixed array compiled into the
+ * library, not in the solver workspace, and the call performs no cudaMalloc,
+ * cudaFree or other allocation.  It is meant for callers that must not
+ * allocate device memory while they run: serving loops that reserve every
+ * byte at admission time (an allocation there can fail or stall under memory
+ * pressure), and programs whose device memory is owned by another allocator
+ * (a raw cudaMalloc would bypass its accounting).  The paper has no
+ * counterpart; this is an integration feature.
+ *   rho  device pointer, [n_elem][(N+1)^dim], copies of shared nodes equal
+ *   mu   device pointer, same layout, written at every copy
+ * Runs on the solver's stream and returns without synchronising.
+ * Limit: n_elem (N+1)^dim <= SEMLBM_NOALLOC_MAX_NODES; larger meshes are
+ * rejected with SEMLBM_EINVAL.  The array (8 MiB) is held by every GPU that
+ * loads the library until the process exits.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  Every call reuses
+ * the same array: each call overwrites all entries it reads, so nothing
+ * carries over between calls, but calls whose work overlaps on the GPU (other
+ * streams, other solvers, other host threads) race on it and must be
+ * serialised by the caller. */
+#define SEMLBM_NOALLOC_MAX_NODES (1 << 20)
+int sem_lbm_chemical_potential_noalloc(sem_lbm_t* s, const double* rho, double* mu);
+
 /* Releases device memory the solver allocated (never the caller's workspace)
  * and the stream it owns.  NULL is ignored. */
 void sem_lbm_destroy(sem_lbm_t* s);

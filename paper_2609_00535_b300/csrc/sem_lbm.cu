@@ -7,6 +7,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <utility>
@@ -221,6 +222,7 @@ struct Carve {
 // ---------------------------------------------------------------------------
 struct sem_lbm {
   int D, N, n, NL, Q, EPB;
+  int device = 0;
   sem_lbm_lattice lat;
   int64_t E, V, G, R;
   double beta, kappa, tau, theta_w, rho_l, rho_v, dt, mu0f;
@@ -260,6 +262,8 @@ struct Ops {
   void (*density)(sem_lbm&);
   void (*velocity)(sem_lbm&, double* u);
   int (*prepare)();
+  void (*lap_into)(sem_lbm&, const double* rho, double* partial);
+  void (*mu_from)(sem_lbm&, const double* partial, const double* rho, double* mu);
 };
 
 namespace {
@@ -352,8 +356,18 @@ struct Impl {
   static void velocity(sem_lbm& s, double* u) {
     k_velocity<L><<<grid_of(s.V, 256), 256, 0, s.stream>>>(s.f, u, s.V);
   }
+  static void lap_into(sem_lbm& s, const double* rho_in, double* partial) {
+    k_lap<L, NP, EPB><<<blocks(s), THREADS, SM_LAP, s.stream>>>(rho_in, s.Gm, wall(s), s.Dm, s.rho_l,
+                                                                s.rho_v, partial, s.V, (int)s.E);
+  }
+  static void mu_from(sem_lbm& s, const double* partial, const double* rho_in, double* mu_out) {
+    k_dss_mu<<<grid_of(s.G, kDssThreads), kDssThreads, 0, s.stream>>>(
+        s.off, s.idx, (int)s.G, partial, rho_in, s.invMg, s.mu0f * s.beta, s.rho_l, s.rho_v,
+        s.kappa, mu_out);
+  }
   static Ops* ops() {
-    static Ops o{geom, wallsetup, lap, mu, force, rhs, collide, rk, diag, init, density, velocity, prepare};
+    static Ops o{geom, wallsetup, lap, mu, force, rhs, collide, rk, diag, init, density, velocity, prepare,
+                 lap_into, mu_from};
     return &o;
   }
 };
@@ -538,6 +552,7 @@ int sem_lbm_create(const sem_lbm_mesh* mesh, int N, sem_lbm_lattice lattice, dou
   if (!s->ops) return bail(fail(SEMLBM_EUNSUPPORTED, "no kernels for N = %d", N));
   if (s->ops->prepare() != 0) return bail(fail(SEMLBM_ECUDA, "cudaFuncSetAttribute failed"));
 
+  if (cudaGetDevice(&s->device) != cudaSuccess) return bail(fail(SEMLBM_ECUDA, "cudaGetDevice failed"));
   if (p.stream) {
     s->stream = (cudaStream_t)p.stream;
   } else {
@@ -738,6 +753,56 @@ int sem_lbm_profile_read(sem_lbm_t* s, sem_lbm_profile_t* out) {
     out->total_ms = ms;
   }
   s->nev = 0;
+  return 0;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free chemical potential: the Laplacian partials go to a fixed
+// device array of the library instead of the solver workspace.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) double g_noalloc_partial[SEMLBM_NOALLOC_MAX_NODES];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+double* g_noalloc_ptr[kMaxDevices] = {};
+
+// device address of g_noalloc_partial on `device`, looked up once per device
+// with that device current (the host-side symbol is only a stand-in)
+int noalloc_scratch(int device, double** out) {
+  if (device < 0 || device >= kMaxDevices) return fail(SEMLBM_EINVAL, "device %d out of range", device);
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[device]) {
+    int prev = 0;
+    CUDA_TRY(cudaGetDevice(&prev));
+    if (prev != device) CUDA_TRY(cudaSetDevice(device));
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partial);
+    if (prev != device) cudaSetDevice(prev);
+    if (e != cudaSuccess) return fail(SEMLBM_ECUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+    g_noalloc_ptr[device] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_ptr[device];
+  return 0;
+}
+}  // namespace
+
+extern "C" {
+
+int sem_lbm_chemical_potential_noalloc(sem_lbm_t* s, const double* rho, double* mu) {
+  if (!s || !rho || !mu) return fail(SEMLBM_EINVAL, "NULL argument");
+  if (s->V > (int64_t)SEMLBM_NOALLOC_MAX_NODES)
+    return fail(SEMLBM_EINVAL,
+                "mesh has %lld element-local nodes; the allocation-free entry point holds at most %d",
+                (long long)s->V, SEMLBM_NOALLOC_MAX_NODES);
+  double* scratch = nullptr;
+  if (int rc = noalloc_scratch(s->device, &scratch)) return rc;
+  // k_lap writes every one of the V partials it then reads: nothing to clear
+  s->ops->lap_into(*s, rho, scratch);
+  s->ops->mu_from(*s, scratch, rho, mu);
+  CUDA_TRY(cudaGetLastError());
   return 0;
 }
 

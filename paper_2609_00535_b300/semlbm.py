@@ -24,7 +24,8 @@ ERRORS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENONFINITE", -5
 EXPORTED = ["sem_lbm_workspace_bytes", "sem_lbm_create", "sem_lbm_set_density", "sem_lbm_step",
             "sem_lbm_diagnostics", "sem_lbm_get_field", "sem_lbm_get_state", "sem_lbm_set_state",
             "sem_lbm_get_info", "sem_lbm_destroy", "sem_lbm_last_error", "sem_lbm_profile",
-            "sem_lbm_profile_read"]
+            "sem_lbm_profile_read", "sem_lbm_chemical_potential_noalloc"]
+NOALLOC_MAX_NODES = 1 << 20
 KERNEL_CLASSES = ["k_lap", "k_dss_mu", "k_force", "k_dss_collide", "k_rhs", "k_dss_rk"]
 PEAK_PATH = os.path.join(_HERE, "libsemlbm_peak.so")
 
@@ -101,6 +102,8 @@ def load():
     L.sem_lbm_last_error.restype = ctypes.c_char_p
     L.sem_lbm_profile.argtypes = [P, I]
     L.sem_lbm_profile_read.argtypes = [P, ctypes.POINTER(ProfileC)]
+    L.sem_lbm_chemical_potential_noalloc.argtypes = [P, P, P]
+    L.sem_lbm_chemical_potential_noalloc.restype = I
     for name in ("sem_lbm_set_density", "sem_lbm_step", "sem_lbm_diagnostics", "sem_lbm_get_field",
                  "sem_lbm_get_state", "sem_lbm_set_state", "sem_lbm_get_info", "sem_lbm_profile",
                  "sem_lbm_profile_read"):
