@@ -30,7 +30,27 @@ sys.path.insert(0, ROOT)
 from paper_2609_00535_b300 import flops as flopcount  # noqa: E402
 from paper_2609_00535_b300 import inputs  # noqa: E402
 
+import hashlib  # noqa: E402
+
 METRIC = "FP64 GLL node-updates/s (3D droplet)"
+
+# DRAM traffic of one k_rhs launch from the ncu capture summarised in
+# profiles/k_rhs_sphere3d_ne12_full.md (373,248 nodes: 76.12 MB read + 8.77 MB
+# written); the traffic grows with the node count, so it is scaled per node.
+# Valid only while the kernel sources are the ones that were profiled.
+RHS_TRAFFIC = {"kernels.cuh": "808e13f9e8afa8d9", "lattice.cuh": "d304ffdc1e4bb53b",
+               "bytes_per_node": (76.120064e6 + 8.773376e6) / 373248, "lattice": "D3Q13", "N": 5}
+
+
+def rhs_traffic_per_launch(lattice, N, n_local):
+    csrc = os.path.join(ROOT, "paper_2609_00535_b300", "csrc")
+    for name in ("kernels.cuh", "lattice.cuh"):
+        h = hashlib.sha256(open(os.path.join(csrc, name), "rb").read()).hexdigest()[:16]
+        if h != RHS_TRAFFIC[name]:
+            return None
+    if (lattice, N) != (RHS_TRAFFIC["lattice"], RHS_TRAFFIC["N"]):
+        return None
+    return RHS_TRAFFIC["bytes_per_node"] * n_local
 UNIT = "node-updates/s"
 L2_BYTES = 126 * 2 ** 20
 
@@ -53,6 +73,23 @@ def sample_case(name):
     if name == "flat2d":
         return inputs.flat_wall_2d(), "the full 1,600-node mesh"
     return inputs.cylinder_2d(n_theta=16, n_r=4), "cylinder O-grid 16x4 elements, N=6"
+
+
+def max_over_ranks(x, device=None):
+    """Max of a float over all ranks (identity at world size 1)."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64,
+                     device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(units_per_rank, seconds_per_rank, world):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return units_per_rank * world / max_over_ranks(seconds_per_rank)
 
 
 def dist_env():
@@ -197,10 +234,7 @@ def native_arm(args):
     ms = e0.elapsed_time(e1)
     prof = solver.profile_read()
     solver.profile(False)
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, device="cuda")
     value = info["n_local"] * args.steps * ws / (ms * 1e-3)
     d = solver.diagnostics()
 
@@ -231,11 +265,7 @@ def native_arm(args):
         solver.step(1)
         solver.diagnostics()
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if ws > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0, device="cuda")
     e2e_value = V * e2e_steps * ws / e2e_s
 
     line = None
@@ -261,7 +291,9 @@ def native_arm(args):
                       (info["workspace_bytes"] / 1e6),
             },
             "roofline": {"bound": "alu", "kernel": "k_rhs", "achieved": achieved, "peak": peak,
-                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "unit": "TFLOP/s", "frac": achieved / peak,
+                         "traffic": rhs_traffic_per_launch(case.lattice, case.mesh.N, V),
+                         "traffic_unit": "bytes per launch",
                          "peak_source": "measured live: FP64 DFMA probe (libsemlbm_peak)",
                          "fp64_op_frac": work["ops"] / (rhs_ms * 1e-3) / (peak * 1e12 / 2),
                          "kernel_ms": rhs_ms, "flops_per_launch": work["flops"]},

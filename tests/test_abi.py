@@ -13,14 +13,23 @@ from paper_2609_00535_b300 import inputs, semlbm
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def declared_symbols():
-    names = set()
-    for fn in os.listdir(os.path.join(ROOT, "include")):
-        if fn.endswith(".h"):
-            txt = open(os.path.join(ROOT, "include", fn)).read()
-            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-            names |= set(re.findall(r"\b(sem_lbm_\w+)\s*\(", txt))
-    return names
+def declared_symbols(header="sem_lbm.h", prefix="sem_lbm_"):
+    txt = open(os.path.join(ROOT, "include", header)).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return set(re.findall(r"\b(%s\w+)\s*\(" % prefix, txt))
+
+
+def test_every_header_is_covered():
+    assert sorted(f for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h")) == \
+        ["sem_lbm.h", "semlbm_peak.h"]
+
+
+def test_peak_library_exports_its_symbol():
+    lib = ctypes.CDLL(semlbm.PEAK_PATH)
+    names = declared_symbols("semlbm_peak.h", "semlbm_")
+    assert names == {"semlbm_fp64_peak"}
+    for n in names:
+        assert hasattr(lib, n)
 
 
 def test_library_exports_every_declared_symbol():
