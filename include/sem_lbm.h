@@ -199,8 +199,55 @@ int sem_lbm_profile_read(sem_lbm_t* s, sem_lbm_profile_t* out);
 #define SEMLBM_NOALLOC_MAX_NODES (1 << 20)
 int sem_lbm_chemical_potential_noalloc(sem_lbm_t* s, const double* rho, double* mu);
 
+/* ---------------------------------------------------------------------------
+ * Batches: many independent solves (uneven meshes, orders, angles) advanced
+ * together.  The paper runs one solve at a time; batching serves its parameter
+ * sweeps (contact angles, geometries).
+ *
+ * A batch owns no solve: sem_lbm_batch_add takes a created, initialised
+ * solver and steps it (sem_lbm_step on it then fails) until it is removed.
+ * While a member, the solver's calls run on the batch's stream.  Solves are
+ * grouped by (velocity set, N), N <= 8; one batch step replays one CUDA graph
+ * whose branches are the groups' persistent kernels over device-resident slot
+ * tables, so adding or removing a member between steps does not re-capture it.
+ * Each member computes exactly the same bits as it would alone.
+ * --------------------------------------------------------------------------- */
+typedef struct sem_lbm_batch sem_lbm_batch_t;
+
+typedef struct {
+  int lattice, N, n_members, epb;     /* epb: elements per CTA in use          */
+  int64_t elem_items, node_items;     /* work-list lengths                      */
+  int grid_elem, grid_node;           /* persistent grid sizes                  */
+  int n_candidates;                   /* tile shapes the tuner can choose from  */
+  int candidate_epb[4];
+  double candidate_ms[4];             /* measured ms per step (0 until tuned)   */
+} sem_lbm_batch_group_info;
+
+/* stream: cudaStream_t or NULL for a batch-owned stream. */
+int sem_lbm_batch_create(void* stream, sem_lbm_batch_t** out);
+/* Adds s (state set, same device, N <= 8); returns its slot index. */
+int sem_lbm_batch_add(sem_lbm_batch_t* b, sem_lbm_t* s, int* slot);
+/* Removes the solver in `slot` (after the batch's pending work). */
+int sem_lbm_batch_remove(sem_lbm_batch_t* b, int slot);
+/* Advances every member n_steps full steps (asynchronous). */
+int sem_lbm_batch_step(sem_lbm_batch_t* b, int64_t n_steps);
+/* Autotuner: for each group, times steps_per_candidate (>= 2) real steps of
+ * every compiled tile shape and keeps the fastest (and remembers it for later
+ * groups of the same velocity set, N and size in this process).  All shapes
+ * give identical results; the tuning steps advance the members like any step. */
+int sem_lbm_batch_tune(sem_lbm_batch_t* b, int steps_per_candidate);
+/* Diagnostics of slots 0..n-1 (one synchronisation); empty slots get
+ * step = -1 and status = SEMLBM_EINVAL. */
+int sem_lbm_batch_diagnostics(sem_lbm_batch_t* b, sem_lbm_diag* out, int n);
+int sem_lbm_batch_info(sem_lbm_batch_t* b, sem_lbm_batch_group_info* out, int max_groups,
+                       int* n_groups);
+/* Slot of a solver in its batch, or -1. */
+int sem_lbm_batch_slot_of(const sem_lbm_t* s);
+/* Removes every member (returning them to their own streams) and frees the batch. */
+void sem_lbm_batch_destroy(sem_lbm_batch_t* b);
+
 /* Releases device memory the solver allocated (never the caller's workspace)
- * and the stream it owns.  NULL is ignored. */
+ * and the stream it owns, after removing it from its batch.  NULL is ignored. */
 void sem_lbm_destroy(sem_lbm_t* s);
 
 /* Message of the calling thread's last failed call ("" if none). */

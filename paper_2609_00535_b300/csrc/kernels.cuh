@@ -27,13 +27,6 @@ namespace semlbm {
 template <int D, int NP, int EPB>
 constexpr int cta_threads() { return ((EPB * ipow(NP, D) + 31) / 32) * 32; }
 
-struct WallDev {
-  const int* slot;     // [V]  wall record of an element-local node, or -1
-  const double* wet;   // [R]  sum over the node's wall faces: w_face |a| cos(theta) sqrt(2 beta/kappa)
-  const double* ae;    // [Q][R] sum over faces of w_face (a . e_alpha) where a . e_alpha < 0
-  int R;
-};
-
 // ---------------------------------------------------------------------------
 // helpers
 // ---------------------------------------------------------------------------
@@ -154,7 +147,7 @@ __global__ void __launch_bounds__(cta_threads<D, NP, EPB>()) k_geom(const double
 }
 
 // assembled mass: invMg[g] = 1 / sum over copies of M_e
-__global__ void k_dss_mass(const int* __restrict__ off, const int* __restrict__ idx, int G,
+static __global__ void k_dss_mass(const int* __restrict__ off, const int* __restrict__ idx, int G,
                            const double* __restrict__ Me, double* __restrict__ invMg) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= G) return;
@@ -228,22 +221,44 @@ __global__ void k_wall_setup(const double* __restrict__ xyz, const double* __res
 }
 
 // ---------------------------------------------------------------------------
+// Everything a time-step kernel needs of one solve.  The single-solve kernels
+// receive it as a kernel parameter; the batched persistent kernels read it
+// from a device-resident slot table.  Both run the same body functions, so a
+// solve computes bit-identical results alone and inside a batch.
+// ---------------------------------------------------------------------------
+struct View {
+  double *f, *fs, *g, *r, *rho, *mu, *lapr, *Fp;   // state and scratch
+  int* flags;                                      // [0] setup, [1] non-finite
+  const double *Jinv, *Gm, *Me, *invMg, *Dm;      // geometry, GLL derivative matrix
+  const int *off, *idx, *wslot;                    // gather-scatter CSR, wall slots
+  const double *wet, *ae;                          // wall records
+  int R, E, G, pad;
+  int64_t V;
+  double dt, omega, kappa, fbeta, rho_l, rho_v;    // omega = 1/(tau + 1/2), fbeta = mu0 factor * beta
+};
+
+// ---------------------------------------------------------------------------
 // a2: element-local weak Laplacian with the wetting wall term, Eq. (weak)
 //     r_i = -sum_b D^T_b [ sum_c G_bc d_c rho ] + wall_i ws cos(theta) sqrt(2b/k)(rl-rho)(rho-rv)
 // ---------------------------------------------------------------------------
 template <class L, int NP, int EPB>
-__global__ void __launch_bounds__(cta_threads<L::D, NP, EPB>()) k_lap(const double* __restrict__ rho, const double* __restrict__ Gm, WallDev w,
-                      const double* __restrict__ Dmat, double rho_l, double rho_v,
-                      double* __restrict__ out, int64_t V, int E) {
+__device__ __forceinline__ void body_lap(const View& v, const double* __restrict__ rho,
+                                         double* __restrict__ out, int eb, double* sm) {
   constexpr int D = L::D, NL = ipow(NP, D), NT = EPB * NL;
-  extern __shared__ double sm[];
+  const int64_t V = v.V;
+  const int E = v.E;
+  const double* __restrict__ Gm = v.Gm;
+  const double* __restrict__ Dmat = v.Dm;
+  const int* __restrict__ wslot = v.wslot;
+  const double* __restrict__ wet = v.wet;
+  const double rho_l = v.rho_l, rho_v = v.rho_v;
   double* sD = sm;
   double* sr = sD + NP * NP;
   double* st = sr + NT;     // [D][NT]
-  const int e0 = blockIdx.x * EPB;
+  const int e0 = eb * EPB;
   const int count = min(EPB, E - e0) * NL;
   const int64_t base = (int64_t)e0 * NL;
-  for (int i = threadIdx.x; i < NP * NP; i += blockDim.x) sD[i] = Dmat[i];
+  for (int i = threadIdx.x; i < NP * NP; i += blockDim.x) sD[i] = __ldg(Dmat + i);
   stage_in(sr, rho, base, count);
   __syncthreads();
   const int tid = threadIdx.x;
@@ -257,108 +272,117 @@ __global__ void __launch_bounds__(cta_threads<L::D, NP, EPB>()) k_lap(const doub
     double g[D];
     grad_ref<D, NP>(Dr, ix, sr + le * NL, k, g);
     if constexpr (D == 2) {
-      const double g00 = Gm[idx], g01 = Gm[V + idx], g11 = Gm[2 * V + idx];
+      const double g00 = __ldg(Gm + idx), g01 = __ldg(Gm + V + idx), g11 = __ldg(Gm + 2 * V + idx);
       st[tid] = fma(g01, g[1], g00 * g[0]);
       st[NT + tid] = fma(g11, g[1], g01 * g[0]);
     } else {
-      const double g00 = Gm[idx], g01 = Gm[V + idx], g02 = Gm[2 * V + idx];
-      const double g11 = Gm[3 * V + idx], g12 = Gm[4 * V + idx], g22 = Gm[5 * V + idx];
+      const double g00 = __ldg(Gm + idx), g01 = __ldg(Gm + V + idx), g02 = __ldg(Gm + 2 * V + idx);
+      const double g11 = __ldg(Gm + 3 * V + idx), g12 = __ldg(Gm + 4 * V + idx);
+      const double g22 = __ldg(Gm + 5 * V + idx);
       st[tid] = fma(g02, g[2], fma(g01, g[1], g00 * g[0]));
       st[NT + tid] = fma(g12, g[2], fma(g11, g[1], g01 * g[0]));
       st[2 * NT + tid] = fma(g22, g[2], fma(g12, g[1], g02 * g[0]));
     }
   }
   __syncthreads();
-  if (!act) return;
-  double Dt[D][NP];
-  load_rows<D, NP>(sD, ix, true, Dt);
-  const int lb = le * NL;
-  double acc = dline<NP, 1>(Dt[0], st + lb + k - ix.i[0]);
-  acc += dline<NP, NP>(Dt[1], st + NT + lb + k - ix.i[1] * NP);
-  if constexpr (D == 3) acc += dline<NP, NP * NP>(Dt[2], st + 2 * NT + lb + k - ix.i[2] * NP * NP);
-  double r = -acc;
-  const int slot = w.slot[idx];
-  if (slot >= 0) {
-    const double rh = sr[lb + k];
-    r = fma(w.wet[slot], (rho_l - rh) * (rh - rho_v), r);
+  if (act) {
+    double Dt[D][NP];
+    load_rows<D, NP>(sD, ix, true, Dt);
+    const int lb = le * NL;
+    double acc = dline<NP, 1>(Dt[0], st + lb + k - ix.i[0]);
+    acc += dline<NP, NP>(Dt[1], st + NT + lb + k - ix.i[1] * NP);
+    if constexpr (D == 3) acc += dline<NP, NP * NP>(Dt[2], st + 2 * NT + lb + k - ix.i[2] * NP * NP);
+    double r = -acc;
+    const int slot = __ldg(wslot + idx);
+    if (slot >= 0) {
+      const double rh = sr[lb + k];
+      r = fma(__ldg(wet + slot), (rho_l - rh) * (rh - rho_v), r);
+    }
+    out[idx] = r;
   }
-  out[idx] = r;
 }
 
 // a3: DSS of the Laplacian partials and the chemical potential, Eq. (chemi)
-__global__ void k_dss_mu(const int* __restrict__ off, const int* __restrict__ idx, int G,
-                         const double* __restrict__ lapr, const double* __restrict__ rho,
-                         const double* __restrict__ invMg, double fbeta, double rho_l,
-                         double rho_v, double kappa, double* __restrict__ mu) {
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= G) return;
+__device__ __forceinline__ void body_dss_mu(const View& v, const double* __restrict__ lapr,
+                                            const double* __restrict__ rho,
+                                            double* __restrict__ mu, int g) {
+  if (g >= v.G) return;
+  const int* __restrict__ off = v.off;
+  const int* __restrict__ idx = v.idx;
+  const double rho_l = v.rho_l, rho_v = v.rho_v;
   const int j0 = off[g], j1 = off[g + 1];
   const int i0 = idx[j0];
   double s = lapr[i0];
   for (int j = j0 + 1; j < j1; ++j) s += lapr[idx[j]];
-  const double lap = s * invMg[g];
+  const double lap = s * __ldg(v.invMg + g);
   const double r = rho[i0];
-  const double m0 = fbeta * (r - rho_l) * (r - rho_v) * (2.0 * r - rho_l - rho_v);
-  const double val = fma(-kappa, lap, m0);
+  const double m0 = v.fbeta * (r - rho_l) * (r - rho_v) * (2.0 * r - rho_l - rho_v);
+  const double val = fma(-v.kappa, lap, m0);
   for (int j = j0; j < j1; ++j) mu[idx[j]] = val;
 }
 
 // a4 (part 1): element-local force M_e (c_s^2 grad rho - rho grad mu) (Sec. 2.1)
 template <class L, int NP, int EPB>
-__global__ void __launch_bounds__(cta_threads<L::D, NP, EPB>()) k_force(const double* __restrict__ rho, const double* __restrict__ mu,
-                        const double* __restrict__ Jinv, const double* __restrict__ Me,
-                        const double* __restrict__ Dmat, double* __restrict__ Fp, int64_t V,
-                        int E) {
+__device__ __forceinline__ void body_force(const View& v, int eb, double* sm) {
   constexpr int D = L::D, NL = ipow(NP, D), NT = EPB * NL;
-  extern __shared__ double sm[];
+  const int64_t V = v.V;
+  const int E = v.E;
+  const double* __restrict__ Jinv = v.Jinv;
+  const double* __restrict__ Me = v.Me;
+  const double* __restrict__ Dmat = v.Dm;
+  double* __restrict__ Fp = v.Fp;
   double* sD = sm;
   double* sr = sD + NP * NP;
   double* smu = sr + NT;
-  const int e0 = blockIdx.x * EPB;
+  const int e0 = eb * EPB;
   const int count = min(EPB, E - e0) * NL;
   const int64_t base = (int64_t)e0 * NL;
-  for (int i = threadIdx.x; i < NP * NP; i += blockDim.x) sD[i] = Dmat[i];
-  stage_in(sr, rho, base, count);
-  stage_in(smu, mu, base, count);
+  for (int i = threadIdx.x; i < NP * NP; i += blockDim.x) sD[i] = __ldg(Dmat + i);
+  stage_in(sr, v.rho, base, count);
+  stage_in(smu, v.mu, base, count);
   __syncthreads();
   const int tid = threadIdx.x;
-  if (tid >= count) return;
-  const int le = tid / NL, k = tid - le * NL;
-  const NodeIdx<D, NP> ix(k);
-  const int64_t idx = base + tid;
-  double Dr[D][NP];
-  load_rows<D, NP>(sD, ix, false, Dr);
-  double dr[D], dm[D];
-  grad_ref<D, NP>(Dr, ix, sr + le * NL, k, dr);
-  grad_ref<D, NP>(Dr, ix, smu + le * NL, k, dm);
-  const double rh = sr[le * NL + k];
-  const double me = Me[idx];
+  if (tid < count) {
+    const int le = tid / NL, k = tid - le * NL;
+    const NodeIdx<D, NP> ix(k);
+    const int64_t idx = base + tid;
+    double Dr[D][NP];
+    load_rows<D, NP>(sD, ix, false, Dr);
+    double dr[D], dm[D];
+    grad_ref<D, NP>(Dr, ix, sr + le * NL, k, dr);
+    grad_ref<D, NP>(Dr, ix, smu + le * NL, k, dm);
+    const double rh = sr[le * NL + k];
+    const double me = __ldg(Me + idx);
 #pragma unroll
-  for (int a = 0; a < D; ++a) {
-    double gr = 0.0, gm = 0.0;
+    for (int a = 0; a < D; ++a) {
+      double gr = 0.0, gm = 0.0;
 #pragma unroll
-    for (int b = 0; b < D; ++b) {
-      const double j = Jinv[(b * D + a) * V + idx];
-      gr = (b == 0) ? j * dr[b] : fma(j, dr[b], gr);
-      gm = (b == 0) ? j * dm[b] : fma(j, dm[b], gm);
+      for (int b = 0; b < D; ++b) {
+        const double j = __ldg(Jinv + (b * D + a) * V + idx);
+        gr = (b == 0) ? j * dr[b] : fma(j, dr[b], gr);
+        gm = (b == 0) ? j * dm[b] : fma(j, dm[b], gm);
+      }
+      Fp[a * V + idx] = me * fma(kCs2, gr, -rh * gm);
     }
-    Fp[a * V + idx] = me * fma(kCs2, gr, -rh * gm);
   }
 }
 
 // a4 (part 2): DSS average of the force and BGK collision with F**
 //   f* = fbar - (fbar - fbar_eq)/(tau + 1/2) + dt F**, fbar_eq = f^eq - dt F**/2
 template <class L>
-__global__ void k_dss_collide(const int* __restrict__ off, const int* __restrict__ idx, int G,
-                              const double* __restrict__ Fp, const double* __restrict__ invMg,
-                              const double* __restrict__ f, const double* __restrict__ rho,
-                              double omega, double dt, double* __restrict__ fs, int64_t V) {
+__device__ __forceinline__ void body_dss_collide(const View& v, int g) {
   constexpr int D = L::D, Q = L::Q;
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= G) return;
+  if (g >= v.G) return;
+  const int64_t V = v.V;
+  const int* __restrict__ off = v.off;
+  const int* __restrict__ idx = v.idx;
+  const double* __restrict__ Fp = v.Fp;
+  const double* __restrict__ f = v.f;
+  double* __restrict__ fs = v.fs;
+  const double omega = v.omega, dt = v.dt;
   const int j0 = off[g], j1 = off[g + 1];
   const int i0 = idx[j0];
-  const double im = invMg[g];
+  const double im = __ldg(v.invMg + g);
   double F[D];
 #pragma unroll
   for (int a = 0; a < D; ++a) {
@@ -369,7 +393,7 @@ __global__ void k_dss_collide(const int* __restrict__ off, const int* __restrict
   double fa[Q];
 #pragma unroll
   for (int q = 0; q < Q; ++q) fa[q] = f[q * V + i0];
-  const double rh = rho[i0];
+  const double rh = v.rho[i0];
   // rho u = sum_a fbar_a e_a (Eq. momentum), via opposite-direction differences
   double m[D];
 #pragma unroll
@@ -424,22 +448,28 @@ __global__ void k_dss_collide(const int* __restrict__ off, const int* __restrict
 //   r_a = M_e [ -e_a . grad(g_a - t_a rho) - (t_a/c_s^2) rho e_a . grad(mu) ]
 //         + flux bounce-back on incoming wall directions (Sec. 2.2)
 template <class L, int NP, int EPB>
-__global__ void __launch_bounds__(cta_threads<L::D, NP, EPB>()) k_rhs(const double* __restrict__ gst, const double* __restrict__ rho,
-                      const double* __restrict__ mu, const double* __restrict__ Jinv,
-                      const double* __restrict__ Me, WallDev w, const double* __restrict__ Dmat,
-                      double* __restrict__ r, int64_t V, int E) {
+__device__ __forceinline__ void body_rhs(const View& v, const double* __restrict__ gst, int eb,
+                                         double* sm) {
   constexpr int D = L::D, Q = L::Q, NL = ipow(NP, D), NT = EPB * NL;
-  extern __shared__ double sm[];
+  const int64_t V = v.V;
+  const int E = v.E;
+  const double* __restrict__ Jinv = v.Jinv;
+  const double* __restrict__ Me = v.Me;
+  const double* __restrict__ Dmat = v.Dm;
+  const int* __restrict__ wslot = v.wslot;
+  const double* __restrict__ wae = v.ae;
+  const int R = v.R;
+  double* __restrict__ r = v.r;
   double* sD = sm;
   double* sr = sD + NP * NP;
   double* smu = sr + NT;
   double* sg = smu + NT;   // [Q-1][NT], moving directions only
-  const int e0 = blockIdx.x * EPB;
+  const int e0 = eb * EPB;
   const int count = min(EPB, E - e0) * NL;
   const int64_t base = (int64_t)e0 * NL;
-  for (int i = threadIdx.x; i < NP * NP; i += blockDim.x) sD[i] = Dmat[i];
-  stage_in(sr, rho, base, count);
-  stage_in(smu, mu, base, count);
+  for (int i = threadIdx.x; i < NP * NP; i += blockDim.x) sD[i] = __ldg(Dmat + i);
+  stage_in(sr, v.rho, base, count);
+  stage_in(smu, v.mu, base, count);
 #pragma unroll 1
   for (int q = 1; q < Q; ++q) stage_in(sg + (q - 1) * NT, gst + q * V, base, count);
   __syncthreads();
@@ -454,37 +484,37 @@ __global__ void __launch_bounds__(cta_threads<L::D, NP, EPB>()) k_rhs(const doub
   grad_ref<D, NP>(Dr, ix, sr + lb, k, dr);
   grad_ref<D, NP>(Dr, ix, smu + lb, k, dm);
   const double rh3 = kInvCs2 * sr[lb + k];
-  double v[D];   // d_b rho - (rho / c_s^2) d_b mu, reference components
+  double vv[D];   // d_b rho - (rho / c_s^2) d_b mu, reference components
 #pragma unroll
-  for (int b = 0; b < D; ++b) v[b] = fma(-rh3, dm[b], dr[b]);
+  for (int b = 0; b < D; ++b) vv[b] = fma(-rh3, dm[b], dr[b]);
   double J[D][D];
 #pragma unroll
   for (int b = 0; b < D; ++b)
 #pragma unroll
-    for (int a = 0; a < D; ++a) J[b][a] = Jinv[(b * D + a) * V + idx];
-  const double ms = Me[idx] * L::S;
-  const int slot = w.slot[idx];
-  static_for<0, L::NREP>([&](auto R) {
-    constexpr int A = L::rep(decltype(R)::value), B = L::opp(A);
+    for (int a = 0; a < D; ++a) J[b][a] = __ldg(Jinv + (b * D + a) * V + idx);
+  const double ms = __ldg(Me + idx) * L::S;
+  const int slot = __ldg(wslot + idx);
+  static_for<0, L::NREP>([&](auto RR) {
+    constexpr int A = L::rep(decltype(RR)::value), B = L::opp(A);
     constexpr double T = L::t(A);
     double c[D];   // (J^-1 C_A)_b: e_A . grad = S sum_b c_b d_b
 #pragma unroll
     for (int b = 0; b < D; ++b) c[b] = L::template cdot<A>(J[b]);
     double dg[D];
     grad_ref<D, NP>(Dr, ix, sg + (A - 1) * NT + lb, k, dg);
-    double s = c[0] * fma(T, v[0], -dg[0]);
+    double s = c[0] * fma(T, vv[0], -dg[0]);
 #pragma unroll
-    for (int b = 1; b < D; ++b) s = fma(c[b], fma(T, v[b], -dg[b]), s);
+    for (int b = 1; b < D; ++b) s = fma(c[b], fma(T, vv[b], -dg[b]), s);
     double rA = ms * s;
     grad_ref<D, NP>(Dr, ix, sg + (B - 1) * NT + lb, k, dg);
-    s = c[0] * fma(T, v[0], -dg[0]);
+    s = c[0] * fma(T, vv[0], -dg[0]);
 #pragma unroll
-    for (int b = 1; b < D; ++b) s = fma(c[b], fma(T, v[b], -dg[b]), s);
+    for (int b = 1; b < D; ++b) s = fma(c[b], fma(T, vv[b], -dg[b]), s);
     double rB = -ms * s;
     if (slot >= 0) {
       const double gA = sg[(A - 1) * NT + lb + k], gB = sg[(B - 1) * NT + lb + k];
-      rA = fma(w.ae[(int64_t)A * w.R + slot], gA - gB, rA);
-      rB = fma(w.ae[(int64_t)B * w.R + slot], gB - gA, rB);
+      rA = fma(__ldg(wae + (int64_t)A * R + slot), gA - gB, rA);
+      rB = fma(__ldg(wae + (int64_t)B * R + slot), gB - gA, rB);
     }
     r[A * V + idx] = rA;
     r[B * V + idx] = rB;
@@ -495,17 +525,20 @@ __global__ void __launch_bounds__(cta_threads<L::D, NP, EPB>()) k_rhs(const doub
 //   stage 1: U1 = U0 + dt L;  stage 2: U2 = 3/4 U0 + 1/4 (U1 + dt L);
 //   stage 3: f^{n+1} = 1/3 U0 + 2/3 (U2 + dt L); rho of the new state
 template <class L, int STAGE>
-__global__ void k_dss_rk(const int* __restrict__ off, const int* __restrict__ idx, int G,
-                         const double* __restrict__ r, const double* __restrict__ invMg,
-                         const double* __restrict__ U0, const double* __restrict__ gcur,
-                         double dt, double* __restrict__ out, double* __restrict__ rho,
-                         int* __restrict__ flag, int64_t V) {
+__device__ __forceinline__ void body_dss_rk(const View& v, const double* __restrict__ gcur,
+                                            double* __restrict__ out, int g) {
   constexpr int Q = L::Q;
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= G) return;
+  if (g >= v.G) return;
+  const int64_t V = v.V;
+  const int* __restrict__ off = v.off;
+  const int* __restrict__ idx = v.idx;
+  const double* __restrict__ r = v.r;
+  const double* __restrict__ U0 = v.fs;
+  double* __restrict__ rho = v.rho;
+  const double dt = v.dt;
   const int j0 = off[g], j1 = off[g + 1];
   const int i0 = idx[j0];
-  const double im = invMg[g];
+  const double im = __ldg(v.invMg + g);
   double val[Q];
   double rs = 0.0;
 #pragma unroll
@@ -517,23 +550,146 @@ __global__ void k_dss_rk(const int* __restrict__ off, const int* __restrict__ id
       Lq = s * im;
     }
     const double u0 = U0[q * V + i0];
-    double v;
+    double x;
     if constexpr (STAGE == 1) {
-      v = fma(dt, Lq, u0);
+      x = fma(dt, Lq, u0);
     } else if constexpr (STAGE == 2) {
-      v = fma(0.25, fma(dt, Lq, gcur[q * V + i0]), 0.75 * u0);
+      x = fma(0.25, fma(dt, Lq, gcur[q * V + i0]), 0.75 * u0);
     } else {
-      v = fma(2.0 / 3.0, fma(dt, Lq, gcur[q * V + i0]), u0 * (1.0 / 3.0));
+      x = fma(2.0 / 3.0, fma(dt, Lq, gcur[q * V + i0]), u0 * (1.0 / 3.0));
     }
-    val[q] = v;
-    rs += v;
+    val[q] = x;
+    rs += x;
   }
-  if (nonfinite(rs)) atomicOr(flag, 1);
+  if (nonfinite(rs)) atomicOr(v.flags + 1, 1);
   for (int j = j0; j < j1; ++j) {
     const int ii = idx[j];
 #pragma unroll
     for (int q = 0; q < Q; ++q) out[q * V + ii] = val[q];
     rho[ii] = rs;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// single-solve kernels: one CTA per element batch / one thread per node group
+// ---------------------------------------------------------------------------
+template <class L, int NP, int EPB>
+__global__ void __launch_bounds__(cta_threads<L::D, NP, EPB>())
+    k_lap(View v, const double* __restrict__ rho, double* __restrict__ out) {
+  extern __shared__ double sm[];
+  body_lap<L, NP, EPB>(v, rho, out, blockIdx.x, sm);
+}
+
+static __global__ void k_dss_mu(View v, const double* __restrict__ lapr, const double* __restrict__ rho,
+                         double* __restrict__ mu) {
+  body_dss_mu(v, lapr, rho, mu, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+template <class L, int NP, int EPB>
+__global__ void __launch_bounds__(cta_threads<L::D, NP, EPB>()) k_force(View v) {
+  extern __shared__ double sm[];
+  body_force<L, NP, EPB>(v, blockIdx.x, sm);
+}
+
+template <class L>
+__global__ void k_dss_collide(View v) {
+  body_dss_collide<L>(v, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+template <class L, int NP, int EPB>
+__global__ void __launch_bounds__(cta_threads<L::D, NP, EPB>())
+    k_rhs(View v, const double* __restrict__ gst) {
+  extern __shared__ double sm[];
+  body_rhs<L, NP, EPB>(v, gst, blockIdx.x, sm);
+}
+
+template <class L, int STAGE>
+__global__ void k_dss_rk(View v, const double* __restrict__ gcur, double* __restrict__ out) {
+  body_dss_rk<L, STAGE>(v, gcur, out, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// ---------------------------------------------------------------------------
+// batched persistent kernels: a fixed grid loops over a device-resident work
+// list of (slot, element batch) or (slot, node-group chunk) items; the slot
+// table and the list live in device memory, so solves can join or leave a
+// batch between launches without re-capturing the CUDA graph
+// ---------------------------------------------------------------------------
+struct WorkItem {
+  int slot, unit;
+};
+
+template <class L, int NP, int EPB>
+__global__ void __launch_bounds__(cta_threads<L::D, NP, EPB>())
+    kb_lap(const View* __restrict__ slots, const WorkItem* __restrict__ items,
+           const int* __restrict__ count) {
+  extern __shared__ double sm[];
+  const int n = *count;
+  for (int w = blockIdx.x; w < n; w += gridDim.x) {
+    const WorkItem it = items[w];
+    const View& v = slots[it.slot];
+    body_lap<L, NP, EPB>(v, v.rho, v.lapr, it.unit, sm);
+    __syncthreads();
+  }
+}
+
+template <class L>
+__global__ void kb_dss_mu(const View* __restrict__ slots, const WorkItem* __restrict__ items,
+                          const int* __restrict__ count) {
+  const int n = *count;
+  for (int w = blockIdx.x; w < n; w += gridDim.x) {
+    const WorkItem it = items[w];
+    const View& v = slots[it.slot];
+    body_dss_mu(v, v.lapr, v.rho, v.mu, it.unit * blockDim.x + threadIdx.x);
+  }
+}
+
+template <class L, int NP, int EPB>
+__global__ void __launch_bounds__(cta_threads<L::D, NP, EPB>())
+    kb_force(const View* __restrict__ slots, const WorkItem* __restrict__ items,
+             const int* __restrict__ count) {
+  extern __shared__ double sm[];
+  const int n = *count;
+  for (int w = blockIdx.x; w < n; w += gridDim.x) {
+    const WorkItem it = items[w];
+    body_force<L, NP, EPB>(slots[it.slot], it.unit, sm);
+    __syncthreads();
+  }
+}
+
+template <class L>
+__global__ void kb_dss_collide(const View* __restrict__ slots, const WorkItem* __restrict__ items,
+                               const int* __restrict__ count) {
+  const int n = *count;
+  for (int w = blockIdx.x; w < n; w += gridDim.x) {
+    const WorkItem it = items[w];
+    body_dss_collide<L>(slots[it.slot], it.unit * blockDim.x + threadIdx.x);
+  }
+}
+
+template <class L, int NP, int EPB>
+__global__ void __launch_bounds__(cta_threads<L::D, NP, EPB>())
+    kb_rhs(const View* __restrict__ slots, const WorkItem* __restrict__ items,
+           const int* __restrict__ count, int from_fs) {
+  extern __shared__ double sm[];
+  const int n = *count;
+  for (int w = blockIdx.x; w < n; w += gridDim.x) {
+    const WorkItem it = items[w];
+    const View& v = slots[it.slot];
+    body_rhs<L, NP, EPB>(v, from_fs ? v.fs : v.g, it.unit, sm);
+    __syncthreads();
+  }
+}
+
+template <class L, int STAGE>
+__global__ void kb_dss_rk(const View* __restrict__ slots, const WorkItem* __restrict__ items,
+                          const int* __restrict__ count) {
+  const int n = *count;
+  for (int w = blockIdx.x; w < n; w += gridDim.x) {
+    const WorkItem it = items[w];
+    const View& v = slots[it.slot];
+    const double* gcur = (STAGE == 1) ? v.fs : v.g;
+    double* out = (STAGE == 3) ? v.f : v.g;
+    body_dss_rk<L, STAGE>(v, gcur, out, it.unit * blockDim.x + threadIdx.x);
   }
 }
 
@@ -592,7 +748,7 @@ __global__ void k_diag(const double* __restrict__ f, const double* __restrict__ 
   if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
 }
 
-__global__ void k_diag_final(const DiagPart* __restrict__ part, int n, DiagPart* __restrict__ out) {
+static __global__ void k_diag_final(const DiagPart* __restrict__ part, int n, DiagPart* __restrict__ out) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   DiagPart a = part[0];
   for (int i = 1; i < n; ++i) {

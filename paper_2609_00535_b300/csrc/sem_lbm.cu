@@ -13,13 +13,11 @@
 #include <utility>
 #include <vector>
 
-#include "kernels.cuh"
-#include "sem_lbm.h"
+#include "solver.cuh"
 
 using namespace semlbm;
 
-namespace {
-
+namespace semlbm {
 thread_local std::string g_err;
 
 int fail(int code, const char* fmt, ...) {
@@ -31,12 +29,9 @@ int fail(int code, const char* fmt, ...) {
   g_err = buf;
   return code;
 }
+}  // namespace semlbm
 
-#define CUDA_TRY(expr)                                                                    \
-  do {                                                                                    \
-    cudaError_t e_ = (expr);                                                              \
-    if (e_ != cudaSuccess) return fail(SEMLBM_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
-  } while (0)
+namespace {
 
 // ---------------------------------------------------------------------------
 // GLL tables in long double.  Nodes: Newton on P_{N+1} - P_{N-1}, whose zeros
@@ -220,57 +215,7 @@ struct Carve {
 }  // namespace
 
 // ---------------------------------------------------------------------------
-struct sem_lbm {
-  int D, N, n, NL, Q, EPB;
-  int device = 0;
-  sem_lbm_lattice lat;
-  int64_t E, V, G, R;
-  double beta, kappa, tau, theta_w, rho_l, rho_v, dt, mu0f;
-  cudaStream_t stream;
-  bool own_stream = false;
-  void* ws = nullptr;
-  bool own_ws = false;
-  size_t ws_bytes = 0;
-  // device arrays
-  double *f, *fs, *g, *r, *rho, *mu, *lapr, *Fp, *Jinv, *Gm, *Me, *invMg, *xyz, *Dm, *wg;
-  int *off, *idx, *slot, *rec_elem, *rec_node, *rec_mask, *flags;
-  double *wet, *ae, *rec_cos;
-  DiagPart *parts, *dout;
-  int diag_blocks = 0;
-  bool state_ready = false;
-  int64_t step = 0;
-  cudaGraphExec_t graph = nullptr;
-  int kernels_per_step = 0;
-  bool prof_on = false;
-  std::vector<cudaEvent_t> ev;   // event pool; ev[0..nev) recorded since the last read
-  std::vector<int> ev_cls;       // class of the kernel that ends at ev[i] (i >= 1)
-  size_t nev = 0;
-  struct Ops* ops = nullptr;
-};
-
-struct Ops {
-  void (*geom)(sem_lbm&);
-  void (*wall)(sem_lbm&);
-  void (*lap)(sem_lbm&);
-  void (*mu)(sem_lbm&);
-  void (*force)(sem_lbm&);
-  void (*rhs)(sem_lbm&, const double* g);
-  void (*collide)(sem_lbm&);
-  void (*rk)(sem_lbm&, int stage, const double* gcur, double* out);
-  void (*diag)(sem_lbm&);
-  void (*init)(sem_lbm&, const double* rho);
-  void (*density)(sem_lbm&);
-  void (*velocity)(sem_lbm&, double* u);
-  int (*prepare)();
-  void (*lap_into)(sem_lbm&, const double* rho, double* partial);
-  void (*mu_from)(sem_lbm&, const double* partial, const double* rho, double* mu);
-};
-
 namespace {
-
-constexpr int kDssThreads = 128;
-
-inline int grid_of(int64_t work, int threads) { return (int)((work + threads - 1) / threads); }
 
 template <class L, int NP>
 struct Impl {
@@ -284,7 +229,6 @@ struct Impl {
   static constexpr size_t SM_GEOM = (NP * NP + D * NT) * sizeof(double);
 
   static int blocks(const sem_lbm& s) { return (int)((s.E + EPB - 1) / EPB); }
-  static WallDev wall(const sem_lbm& s) { return WallDev{s.slot, s.wet, s.ae, (int)s.R}; }
 
   static int prepare() {
     // opt in to large dynamic shared memory where a tile needs it
@@ -311,37 +255,28 @@ struct Impl {
         std::sqrt(2.0 * s.beta / s.kappa), s.wet, s.ae);
   }
   static void lap(sem_lbm& s) {
-    k_lap<L, NP, EPB><<<blocks(s), THREADS, SM_LAP, s.stream>>>(s.rho, s.Gm, wall(s), s.Dm, s.rho_l,
-                                                                s.rho_v, s.lapr, s.V, (int)s.E);
+    k_lap<L, NP, EPB><<<blocks(s), THREADS, SM_LAP, s.stream>>>(s.view, s.rho, s.lapr);
   }
   static void mu(sem_lbm& s) {
-    k_dss_mu<<<grid_of(s.G, kDssThreads), kDssThreads, 0, s.stream>>>(
-        s.off, s.idx, (int)s.G, s.lapr, s.rho, s.invMg, s.mu0f * s.beta, s.rho_l, s.rho_v, s.kappa,
-        s.mu);
+    k_dss_mu<<<grid_of(s.G, kDssThreads), kDssThreads, 0, s.stream>>>(s.view, s.lapr, s.rho, s.mu);
   }
   static void force(sem_lbm& s) {
-    k_force<L, NP, EPB><<<blocks(s), THREADS, SM_FORCE, s.stream>>>(s.rho, s.mu, s.Jinv, s.Me, s.Dm,
-                                                                    s.Fp, s.V, (int)s.E);
+    k_force<L, NP, EPB><<<blocks(s), THREADS, SM_FORCE, s.stream>>>(s.view);
   }
   static void collide(sem_lbm& s) {
-    k_dss_collide<L><<<grid_of(s.G, kDssThreads), kDssThreads, 0, s.stream>>>(
-        s.off, s.idx, (int)s.G, s.Fp, s.invMg, s.f, s.rho, 1.0 / (s.tau + 0.5), s.dt, s.fs, s.V);
+    k_dss_collide<L><<<grid_of(s.G, kDssThreads), kDssThreads, 0, s.stream>>>(s.view);
   }
   static void rhs(sem_lbm& s, const double* gst) {
-    k_rhs<L, NP, EPB><<<blocks(s), THREADS, SM_RHS, s.stream>>>(gst, s.rho, s.mu, s.Jinv, s.Me,
-                                                                wall(s), s.Dm, s.r, s.V, (int)s.E);
+    k_rhs<L, NP, EPB><<<blocks(s), THREADS, SM_RHS, s.stream>>>(s.view, gst);
   }
   static void rk(sem_lbm& s, int stage, const double* gcur, double* out) {
     const int gr = grid_of(s.G, kDssThreads);
     if (stage == 1)
-      k_dss_rk<L, 1><<<gr, kDssThreads, 0, s.stream>>>(s.off, s.idx, (int)s.G, s.r, s.invMg, s.fs,
-                                                       gcur, s.dt, out, s.rho, s.flags + 1, s.V);
+      k_dss_rk<L, 1><<<gr, kDssThreads, 0, s.stream>>>(s.view, gcur, out);
     else if (stage == 2)
-      k_dss_rk<L, 2><<<gr, kDssThreads, 0, s.stream>>>(s.off, s.idx, (int)s.G, s.r, s.invMg, s.fs,
-                                                       gcur, s.dt, out, s.rho, s.flags + 1, s.V);
+      k_dss_rk<L, 2><<<gr, kDssThreads, 0, s.stream>>>(s.view, gcur, out);
     else
-      k_dss_rk<L, 3><<<gr, kDssThreads, 0, s.stream>>>(s.off, s.idx, (int)s.G, s.r, s.invMg, s.fs,
-                                                       gcur, s.dt, out, s.rho, s.flags + 1, s.V);
+      k_dss_rk<L, 3><<<gr, kDssThreads, 0, s.stream>>>(s.view, gcur, out);
   }
   static void diag(sem_lbm& s) {
     k_diag<L><<<s.diag_blocks, 256, 0, s.stream>>>(s.f, s.Me, s.parts, s.V);
@@ -357,13 +292,11 @@ struct Impl {
     k_velocity<L><<<grid_of(s.V, 256), 256, 0, s.stream>>>(s.f, u, s.V);
   }
   static void lap_into(sem_lbm& s, const double* rho_in, double* partial) {
-    k_lap<L, NP, EPB><<<blocks(s), THREADS, SM_LAP, s.stream>>>(rho_in, s.Gm, wall(s), s.Dm, s.rho_l,
-                                                                s.rho_v, partial, s.V, (int)s.E);
+    k_lap<L, NP, EPB><<<blocks(s), THREADS, SM_LAP, s.stream>>>(s.view, rho_in, partial);
   }
   static void mu_from(sem_lbm& s, const double* partial, const double* rho_in, double* mu_out) {
-    k_dss_mu<<<grid_of(s.G, kDssThreads), kDssThreads, 0, s.stream>>>(
-        s.off, s.idx, (int)s.G, partial, rho_in, s.invMg, s.mu0f * s.beta, s.rho_l, s.rho_v,
-        s.kappa, mu_out);
+    k_dss_mu<<<grid_of(s.G, kDssThreads), kDssThreads, 0, s.stream>>>(s.view, partial, rho_in,
+                                                                      mu_out);
   }
   static Ops* ops() {
     static Ops o{geom, wallsetup, lap, mu, force, rhs, collide, rk, diag, init, density, velocity, prepare,
@@ -458,6 +391,23 @@ size_t layout(sem_lbm& s, char* base) {
   s.parts = c.take<DiagPart>(s.diag_blocks);
   s.dout = c.take<DiagPart>(1);
   return c.off;
+}
+
+void fill_view(sem_lbm& s) {
+  View& v = s.view;
+  v.f = s.f; v.fs = s.fs; v.g = s.g; v.r = s.r;
+  v.rho = s.rho; v.mu = s.mu; v.lapr = s.lapr; v.Fp = s.Fp;
+  v.flags = s.flags;
+  v.Jinv = s.Jinv; v.Gm = s.Gm; v.Me = s.Me; v.invMg = s.invMg; v.Dm = s.Dm;
+  v.off = s.off; v.idx = s.idx; v.wslot = s.slot; v.wet = s.wet; v.ae = s.ae;
+  v.R = (int)s.R; v.E = (int)s.E; v.G = (int)s.G; v.pad = 0;
+  v.V = s.V;
+  v.dt = s.dt;
+  v.omega = 1.0 / (s.tau + 0.5);
+  v.kappa = s.kappa;
+  v.fbeta = s.mu0f * s.beta;
+  v.rho_l = s.rho_l;
+  v.rho_v = s.rho_v;
 }
 
 int diag_blocks_for(int64_t V) { return (int)std::min<int64_t>(1184, (V + 255) / 256); }
@@ -575,6 +525,7 @@ int sem_lbm_create(const sem_lbm_mesh* mesh, int N, sem_lbm_lattice lattice, dou
     s->own_ws = true;
   }
   layout(*s, (char*)s->ws);
+  fill_view(*s);
 
   std::vector<double> x, w, Dm;
   gll_tables(N, x, w, Dm);
@@ -633,6 +584,7 @@ int sem_lbm_step(sem_lbm_t* s, int64_t n_steps) {
   if (!s) return fail(SEMLBM_EINVAL, "NULL solver");
   if (n_steps < 0) return fail(SEMLBM_EINVAL, "n_steps must be >= 0");
   if (!s->state_ready) return fail(SEMLBM_EINVAL, "state not set (call sem_lbm_set_density)");
+  if (s->batch) return fail(SEMLBM_EINVAL, "solver is stepped by its batch (sem_lbm_batch_step)");
   if (n_steps == 0) return 0;
   if (s->prof_on) {
     if (s->nev == 0 && !record_event(*s, -1)) return fail(SEMLBM_ECUDA, "cudaEventRecord failed");
@@ -808,6 +760,7 @@ int sem_lbm_chemical_potential_noalloc(sem_lbm_t* s, const double* rho, double* 
 
 void sem_lbm_destroy(sem_lbm_t* s) {
   if (!s) return;
+  if (s->batch) sem_lbm_batch_remove(s->batch, sem_lbm_batch_slot_of(s));
   if (s->stream) cudaStreamSynchronize(s->stream);
   for (cudaEvent_t e : s->ev) cudaEventDestroy(e);
   if (s->graph) cudaGraphExecDestroy(s->graph);

@@ -1,0 +1,81 @@
+// Private to libsemlbm: the solver object shared by the single-solve C ABI
+// (sem_lbm.cu) and the batch engine (batch.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+#include "sem_lbm.h"
+
+namespace semlbm {
+
+// records a message for sem_lbm_last_error() and returns code
+int fail(int code, const char* fmt, ...);
+
+constexpr int kDssThreads = 128;   // threads per CTA of the gather-scatter kernels
+
+inline int grid_of(int64_t work, int threads) { return (int)((work + threads - 1) / threads); }
+
+}  // namespace semlbm
+
+#define CUDA_TRY(expr)                                                                      \
+  do {                                                                                      \
+    cudaError_t e_ = (expr);                                                                \
+    if (e_ != cudaSuccess)                                                                  \
+      return semlbm::fail(SEMLBM_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_));           \
+  } while (0)
+
+struct sem_lbm_batch;
+
+struct sem_lbm {
+  int D, N, n, NL, Q, EPB;
+  int device = 0;
+  sem_lbm_lattice lat;
+  int64_t E, V, G, R;
+  double beta, kappa, tau, theta_w, rho_l, rho_v, dt, mu0f;
+  cudaStream_t stream;
+  bool own_stream = false;
+  void* ws = nullptr;
+  bool own_ws = false;
+  size_t ws_bytes = 0;
+  // device arrays
+  double *f, *fs, *g, *r, *rho, *mu, *lapr, *Fp, *Jinv, *Gm, *Me, *invMg, *xyz, *Dm, *wg;
+  int *off, *idx, *slot, *rec_elem, *rec_node, *rec_mask, *flags;
+  double *wet, *ae, *rec_cos;
+  semlbm::DiagPart *parts, *dout;
+  int diag_blocks = 0;
+  bool state_ready = false;
+  int64_t step = 0;
+  semlbm::View view{};                   // device pointers + parameters, for the kernels
+  cudaGraphExec_t graph = nullptr;
+  int kernels_per_step = 0;
+  bool prof_on = false;
+  sem_lbm_batch* batch = nullptr;     // set while a batch steps this solver
+  cudaStream_t home_stream = nullptr; // the solver's own stream while it is in a batch
+  std::vector<cudaEvent_t> ev;   // event pool; ev[0..nev) recorded since the last read
+  std::vector<int> ev_cls;       // class of the kernel that ends at ev[i] (i >= 1)
+  size_t nev = 0;
+  struct Ops* ops = nullptr;
+};
+
+struct Ops {
+  void (*geom)(sem_lbm&);
+  void (*wall)(sem_lbm&);
+  void (*lap)(sem_lbm&);
+  void (*mu)(sem_lbm&);
+  void (*force)(sem_lbm&);
+  void (*rhs)(sem_lbm&, const double* g);
+  void (*collide)(sem_lbm&);
+  void (*rk)(sem_lbm&, int stage, const double* gcur, double* out);
+  void (*diag)(sem_lbm&);
+  void (*init)(sem_lbm&, const double* rho);
+  void (*density)(sem_lbm&);
+  void (*velocity)(sem_lbm&, double* u);
+  int (*prepare)();
+  void (*lap_into)(sem_lbm&, const double* rho, double* partial);
+  void (*mu_from)(sem_lbm&, const double* partial, const double* rho, double* mu);
+};
+

@@ -24,7 +24,10 @@ ERRORS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENONFINITE", -5
 EXPORTED = ["sem_lbm_workspace_bytes", "sem_lbm_create", "sem_lbm_set_density", "sem_lbm_step",
             "sem_lbm_diagnostics", "sem_lbm_get_field", "sem_lbm_get_state", "sem_lbm_set_state",
             "sem_lbm_get_info", "sem_lbm_destroy", "sem_lbm_last_error", "sem_lbm_profile",
-            "sem_lbm_profile_read", "sem_lbm_chemical_potential_noalloc"]
+            "sem_lbm_profile_read", "sem_lbm_chemical_potential_noalloc",
+            "sem_lbm_batch_create", "sem_lbm_batch_add", "sem_lbm_batch_remove",
+            "sem_lbm_batch_step", "sem_lbm_batch_tune", "sem_lbm_batch_diagnostics",
+            "sem_lbm_batch_info", "sem_lbm_batch_slot_of", "sem_lbm_batch_destroy"]
 NOALLOC_MAX_NODES = 1 << 20
 KERNEL_CLASSES = ["k_lap", "k_dss_mu", "k_force", "k_dss_collide", "k_rhs", "k_dss_rk"]
 PEAK_PATH = os.path.join(_HERE, "libsemlbm_peak.so")
@@ -72,6 +75,14 @@ class InfoC(ctypes.Structure):
                 ("graph_launches", ctypes.c_int), ("kernels_per_step", ctypes.c_int)]
 
 
+class GroupInfoC(ctypes.Structure):
+    _fields_ = [("lattice", ctypes.c_int), ("N", ctypes.c_int), ("n_members", ctypes.c_int),
+                ("epb", ctypes.c_int), ("elem_items", ctypes.c_int64),
+                ("node_items", ctypes.c_int64), ("grid_elem", ctypes.c_int),
+                ("grid_node", ctypes.c_int), ("n_candidates", ctypes.c_int),
+                ("candidate_epb", ctypes.c_int * 4), ("candidate_ms", ctypes.c_double * 4)]
+
+
 _lib = None
 
 
@@ -104,6 +115,20 @@ def load():
     L.sem_lbm_profile_read.argtypes = [P, ctypes.POINTER(ProfileC)]
     L.sem_lbm_chemical_potential_noalloc.argtypes = [P, P, P]
     L.sem_lbm_chemical_potential_noalloc.restype = I
+    L.sem_lbm_batch_create.argtypes = [P, ctypes.POINTER(P)]
+    L.sem_lbm_batch_add.argtypes = [P, P, ctypes.POINTER(I)]
+    L.sem_lbm_batch_remove.argtypes = [P, I]
+    L.sem_lbm_batch_step.argtypes = [P, I64]
+    L.sem_lbm_batch_tune.argtypes = [P, I]
+    L.sem_lbm_batch_diagnostics.argtypes = [P, ctypes.POINTER(DiagC), I]
+    L.sem_lbm_batch_info.argtypes = [P, ctypes.POINTER(GroupInfoC), I, ctypes.POINTER(I)]
+    L.sem_lbm_batch_slot_of.argtypes = [P]
+    L.sem_lbm_batch_destroy.argtypes = [P]
+    L.sem_lbm_batch_destroy.restype = None
+    for name in ("sem_lbm_batch_create", "sem_lbm_batch_add", "sem_lbm_batch_remove",
+                 "sem_lbm_batch_step", "sem_lbm_batch_tune", "sem_lbm_batch_diagnostics",
+                 "sem_lbm_batch_info", "sem_lbm_batch_slot_of"):
+        getattr(L, name).restype = I
     for name in ("sem_lbm_set_density", "sem_lbm_step", "sem_lbm_diagnostics", "sem_lbm_get_field",
                  "sem_lbm_get_state", "sem_lbm_set_state", "sem_lbm_get_info", "sem_lbm_profile",
                  "sem_lbm_profile_read"):
@@ -266,6 +291,76 @@ class Solver:
     def close(self):
         if getattr(self, "h", None):
             load().sem_lbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Several solves stepped together (see sem_lbm_batch_* in sem_lbm.h)."""
+
+    def __init__(self, stream=None, device=0):
+        import torch
+        self.device = torch.device("cuda", device)
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            check(load().sem_lbm_batch_create(self.stream.cuda_stream, ctypes.byref(h)))
+        self.h = h
+        self.members = {}
+
+    def add(self, solver):
+        slot = ctypes.c_int()
+        check(load().sem_lbm_batch_add(self.h, solver.h, ctypes.byref(slot)))
+        self.members[slot.value] = solver
+        solver.batch = self
+        return slot.value
+
+    def remove(self, slot):
+        check(load().sem_lbm_batch_remove(self.h, int(slot)))
+        s = self.members.pop(slot)
+        s.batch = None
+        return s
+
+    def step(self, n=1):
+        check(load().sem_lbm_batch_step(self.h, int(n)))
+
+    def tune(self, steps_per_candidate=3):
+        check(load().sem_lbm_batch_tune(self.h, int(steps_per_candidate)))
+
+    def diagnostics(self):
+        n = max(self.members) + 1 if self.members else 0
+        arr = (DiagC * max(n, 1))()
+        check(load().sem_lbm_batch_diagnostics(self.h, arr, n))
+        return {i: {k: getattr(arr[i], k) for k, _ in DiagC._fields_} for i in self.members}
+
+    def info(self):
+        arr = (GroupInfoC * 32)()
+        ng = ctypes.c_int()
+        check(load().sem_lbm_batch_info(self.h, arr, 32, ctypes.byref(ng)))
+        out = []
+        for i in range(min(ng.value, 32)):
+            g = arr[i]
+            out.append({"lattice": g.lattice, "N": g.N, "n_members": g.n_members, "epb": g.epb,
+                        "elem_items": g.elem_items, "node_items": g.node_items,
+                        "grid_elem": g.grid_elem, "grid_node": g.grid_node,
+                        "candidates": [(g.candidate_epb[c], g.candidate_ms[c])
+                                       for c in range(g.n_candidates)]})
+        return out
+
+    def synchronize(self):
+        self.stream.synchronize()
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().sem_lbm_batch_destroy(self.h)
+            for s in self.members.values():
+                s.batch = None
+            self.members = {}
             self.h = None
 
     def __del__(self):
