@@ -187,6 +187,80 @@ def reference_arm(args):
     return 0
 
 
+def batched_section(args, device):
+    """64 solves of uneven E, N and angle: 64 sequential plain solves against one
+    autotuned batch (every solve advances the same number of steps in both)."""
+    import torch
+    from paper_2609_00535_b300 import semlbm
+    cases = inputs.batch_mix(n=args.batch_solves, seed=4)
+    solvers = []
+    for c in cases:
+        s = semlbm.Solver.from_case(c, device=device)
+        s.set_density(c.rho0)
+        solvers.append(s)
+    nodes = sum(s.info["n_local"] for s in solvers)
+    K = args.batch_steps
+    for s in solvers:                       # warm-up, graph capture
+        s.step(2)
+        s.synchronize()
+    t0 = time.perf_counter()
+    for s in solvers:                       # plain: one solve after the other
+        s.step(K)
+        s.synchronize()
+    t_plain = time.perf_counter() - t0
+    b = semlbm.Batch(device=device)
+    for s in solvers:
+        b.add(s)
+    t0 = time.perf_counter()
+    b.tune(3)
+    t_tune = time.perf_counter() - t0
+    b.step(2)
+    b.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    e0.record(b.stream)
+    b.step(K)
+    e1.record(b.stream)
+    b.synchronize()
+    t_batch_host = time.perf_counter() - t0
+    t_batch = e0.elapsed_time(e1) * 1e-3
+    groups = b.info()
+    diag = b.diagnostics()
+    ok = all(d["status"] == 0 for d in diag.values())
+    b.close()
+    for s in solvers:
+        s.close()
+    return {"solves": len(cases), "nodes": nodes, "steps": K,
+            "plain_node_updates_per_s": nodes * K / t_plain,
+            "batched_node_updates_per_s": nodes * K / t_batch,
+            "batched_host_clock_node_updates_per_s": nodes * K / t_batch_host,
+            "speedup": t_plain / t_batch, "tune_s": t_tune, "all_finite": ok,
+            "groups": [{"lattice": ["D2Q9", "D3Q13"][g["lattice"]], "N": g["N"],
+                        "members": g["n_members"], "epb": g["epb"],
+                        "candidates": g["candidates"]} for g in groups]}
+
+
+def serving_section(args, device, capacity):
+    """Poisson stream of sweep requests through the continuous-batching server."""
+    from paper_2609_00535_b300 import serve
+    n = args.serve_requests
+    probe = inputs.request_stream(n=n, rate=1.0, seed=5)
+    nodes = [r.E * (r.N + 1) ** (3 if "3d" in r.kind else 2) for r in probe]
+    work = sum(nodes) / len(nodes) * args.serve_max_steps
+    rate = 1.2 * capacity / work              # offered load 1.2x the measured capacity
+    reqs = inputs.request_stream(n=n, rate=rate, seed=5)
+    srv = serve.Server(hbm_budget_bytes=int(args.serve_budget_gb * 2 ** 30),
+                       epoch_steps=args.serve_epoch, ke_tol=1e-20,
+                       max_steps=args.serve_max_steps, min_steps=args.serve_epoch)
+    st = srv.run(reqs)
+    out = st.summary()
+    out.update({"arrival_rate_per_s": rate, "offered_load": 1.2, "ke_tol": 1e-20,
+                "max_steps": args.serve_max_steps, "epoch_steps": args.serve_epoch,
+                "hbm_budget_gb": args.serve_budget_gb})
+    return out
+
+
 def native_arm(args):
     import numpy as np
     import torch
@@ -277,6 +351,12 @@ def native_arm(args):
             cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                    "sample": "%d time steps of the full %s mesh (%d nodes), %.1f s" %
                              (cpu_steps, args.config, case.nodes, secs)}
+        batched = serving = None
+        if not args.no_batched:
+            batched = batched_section(args, device)
+        if not args.no_serving:
+            cap = batched["batched_node_updates_per_s"] if batched else value
+            serving = serving_section(args, device, cap)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -303,6 +383,8 @@ def native_arm(args):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": Q * V * 8,
                     "d2h_bytes_per_step": 80, "steps": e2e_steps},
             "cpu_baseline": cpu,
+            "batched": batched,
+            "serving": serving,
             "final_diag": {"ke_max": d["ke_max"], "mass": d["mass"], "status": d["status"]},
         }
         print(json.dumps(line), flush=True)
@@ -321,6 +403,14 @@ def main():
     ap.add_argument("--config", default="sphere3d", choices=["sphere3d", "flat2d", "cylinder2d"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=3)
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--batch-solves", type=int, default=64)
+    ap.add_argument("--batch-steps", type=int, default=20)
+    ap.add_argument("--serve-requests", type=int, default=100)
+    ap.add_argument("--serve-max-steps", type=int, default=300)
+    ap.add_argument("--serve-epoch", type=int, default=50)
+    ap.add_argument("--serve-budget-gb", type=float, default=40.0)
     ap.add_argument("--ne", type=int, default=None,
                     help="elements per axis of the sphere-cap mesh (profiling cases only)")
     args = ap.parse_args()

@@ -376,3 +376,89 @@ def periodic_droplet(dim=2, ne=4, N=8, L=1.0, D=0.5, Cn=0.063, beta=1e-3, tau=0.
     rho0 = droplet_density(mesh, (L / 2,) * dim, D / 2, delta, rho_l, rho_v)
     return Case("droplet%dd" % dim, mesh, lat, rho_l, rho_v, beta, kappa, tau,
                 cfl_dt(mesh, lat, cfl, kappa, rho_l), math.pi / 2, (), rho0, steps, {"delta": delta})
+
+
+# ---------------------------------------------------------------------------
+# Mixed workloads for batching and serving (uneven meshes, orders and angles).
+# ---------------------------------------------------------------------------
+def _log_uniform_int(rng, lo, hi):
+    return int(round(math.exp(rng.uniform(math.log(lo), math.log(hi)))))
+
+
+def mixed_case(rng, kind, E, N, theta, radius_scale=1.0):
+    """One solve of the given kind with about E elements (rounded to the generator's grid)."""
+    if kind == "flat2d":
+        a = max(2, int(round(math.sqrt(E))))
+        b = max(2, int(round(E / a)))
+        c = flat_wall_2d(N=N, ne=(a, b), theta=theta, R=0.25 * radius_scale)
+    elif kind == "cylinder2d":
+        n_r = max(2, int(round(math.sqrt(E / 4.0))))
+        n_t = max(8, int(round(E / n_r)))
+        c = cylinder_2d(theta=theta, N=N, n_theta=n_t, n_r=n_r, seed=int(rng.integers(1 << 30)),
+                        perm_seed=int(rng.integers(1 << 30)))
+    elif kind == "sphere3d":
+        ne = max(2, int(round(E ** (1.0 / 3.0))))
+        c = sphere_3d(N=N, ne=(ne, ne, ne), theta=theta, d=0.25 * radius_scale)
+    elif kind == "droplet2d":
+        ne = max(2, int(round(math.sqrt(E))))
+        c = periodic_droplet(dim=2, ne=ne, N=N, D=0.5 * radius_scale, Cn=max(0.063, 4.0 / (ne * N)))
+    elif kind == "droplet3d":
+        ne = max(2, int(round(E ** (1.0 / 3.0))))
+        c = periodic_droplet(dim=3, ne=ne, N=N, D=0.5 * radius_scale, Cn=max(0.063, 4.0 / (ne * N)))
+    else:
+        raise ValueError(kind)
+    c.name = "%s-E%d-N%d-%.0fdeg" % (kind, c.mesh.n_elem, N, math.degrees(theta))
+    return c
+
+
+def batch_mix(n=64, seed=4, elems=(256, 4096), orders=(4, 5, 6, 7, 8)):
+    """Batched workload: n solves, E log-uniform, N uniform, theta uniform in
+    [15, 165] degrees, 2D/3D half and half (flat wall or cylinder in 2D, sphere
+    cap in 3D)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        E = _log_uniform_int(rng, *elems)
+        N = int(rng.choice(orders))
+        theta = math.radians(rng.uniform(15.0, 165.0))
+        if rng.random() < 0.5:
+            kind = "flat2d" if rng.random() < 0.5 else "cylinder2d"
+        else:
+            kind = "sphere3d"
+        out.append(mixed_case(rng, kind, E, N, theta))
+    return out
+
+
+@dataclass
+class Request:
+    rid: int
+    arrival: float         # seconds after the start of the stream
+    kind: str
+    E: int
+    N: int
+    theta: float
+    radius_scale: float
+    seed: int
+
+    def case(self):
+        return mixed_case(np.random.default_rng(self.seed), self.kind, self.E, self.N, self.theta,
+                          self.radius_scale)
+
+
+def request_stream(n=500, rate=10.0, seed=5, elems=(256, 8192), orders=(4, 5, 6, 7)):
+    """Poisson arrivals of sweep requests: a quarter each of 2D flat wall, 2D
+    cylinder, 3D sphere cap and isolated periodic droplet (2D or 3D), E
+    log-uniform, N uniform, random contact angle and drop radius."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    kinds = ["flat2d", "cylinder2d", "sphere3d", "droplet"]
+    out = []
+    for i in range(n):
+        t += rng.exponential(1.0 / rate)
+        kind = kinds[i % 4]
+        if kind == "droplet":
+            kind = "droplet2d" if rng.random() < 0.5 else "droplet3d"
+        out.append(Request(i, t, kind, _log_uniform_int(rng, *elems), int(rng.choice(orders)),
+                           math.radians(rng.uniform(15.0, 165.0)), float(rng.uniform(0.8, 1.2)),
+                           int(rng.integers(1 << 30))))
+    return out

@@ -1,0 +1,41 @@
+"""Serving: requests admitted while others run produce exactly the results
+they produce alone."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2609_00535_b300 import inputs
+from paper_2609_00535_b300.serve import Server
+
+pytestmark = pytest.mark.gpu
+
+
+def test_continuous_batching_equals_alone():
+    from paper_2609_00535_b300 import semlbm
+    kinds = ["flat2d", "cylinder2d", "sphere3d", "droplet2d", "droplet3d", "flat2d"]
+    reqs = [inputs.Request(i, 0.04 * i, k, 64 if "3d" in k else 96, 4 + i % 3,
+                           math.radians(20 + 25 * i), 1.0, 1000 + i) for i, k in enumerate(kinds)]
+    srv = Server(hbm_budget_bytes=4 << 30, epoch_steps=20, ke_tol=0.0, max_steps=100,
+                 min_steps=20, keep_state=True, workers=3)
+    st = srv.run(reqs)
+    summ = st.summary()
+    assert summ["completed"] == len(reqs) and summ["failed"] == 0
+    assert summ["max_slots"] >= 2 and summ["overlapped_admissions"] >= 1
+    for req, rec in zip(reqs, st.records):
+        assert rec.steps >= 100 and rec.state is not None
+        case = req.case()
+        s = semlbm.Solver.from_case(case)
+        s.set_density(case.rho0)
+        s.step(rec.steps)
+        assert np.array_equal(s.get_state()[0], rec.state), rec.name
+        s.close()
+
+
+def test_budget_limits_concurrent_slots():
+    reqs = [inputs.Request(i, 0.0, "flat2d", 64, 4, math.radians(60), 1.0, i) for i in range(4)]
+    from paper_2609_00535_b300 import semlbm
+    one = semlbm.workspace_bytes(reqs[0].case().mesh, 4, "D2Q9")
+    st = Server(hbm_budget_bytes=int(1.5 * one), epoch_steps=10, ke_tol=0.0, max_steps=30,
+                min_steps=10).run(reqs)
+    assert st.summary()["completed"] == 4 and st.max_slots == 1
