@@ -57,6 +57,29 @@ __device__ __forceinline__ void grad_ref(const double (&Dr)[D][NP], const NodeId
   if constexpr (D == 3) out[2] = dline<NP, NP * NP>(Dr[2], tile + k - ix.i[2] * NP * NP);
 }
 
+// reference gradients of two tiles at node k, as 2D independent chains
+template <int D, int NP>
+__device__ __forceinline__ void grad_ref2(const double (&Dr)[D][NP], const NodeIdx<D, NP>& ix,
+                                          const double* __restrict__ ta,
+                                          const double* __restrict__ tb, int k, double (&oa)[D],
+                                          double (&ob)[D]) {
+  constexpr int st[3] = {1, NP, NP * NP};
+  int k0[D];
+#pragma unroll
+  for (int b = 0; b < D; ++b) {
+    k0[b] = k - ix.i[b] * st[b];
+    oa[b] = Dr[b][0] * ta[k0[b]];
+    ob[b] = Dr[b][0] * tb[k0[b]];
+  }
+#pragma unroll
+  for (int m = 1; m < NP; ++m)
+#pragma unroll
+    for (int b = 0; b < D; ++b) {
+      oa[b] = fma(Dr[b][m], ta[k0[b] + m * st[b]], oa[b]);
+      ob[b] = fma(Dr[b][m], tb[k0[b] + m * st[b]], ob[b]);
+    }
+}
+
 template <int D, int NP>
 __device__ __forceinline__ void load_rows(const double* __restrict__ sD, const NodeIdx<D, NP>& ix,
                                           bool transpose, double (&Dr)[D][NP]) {
@@ -228,6 +251,7 @@ __global__ void k_wall_setup(const double* __restrict__ xyz, const double* __res
 // ---------------------------------------------------------------------------
 struct View {
   double *f, *fs, *g, *r, *rho, *mu, *lapr, *Fp;   // state and scratch
+  double* drho;                                    // [D][V] reference gradient of rho (k_lap)
   int* flags;                                      // [0] setup, [1] non-finite
   const double *Jinv, *Gm, *Me, *invMg, *Dm;      // geometry, GLL derivative matrix
   const int *off, *idx, *wslot;                    // gather-scatter CSR, wall slots
@@ -243,7 +267,8 @@ struct View {
 // ---------------------------------------------------------------------------
 template <class L, int NP, int EPB>
 __device__ __forceinline__ void body_lap(const View& v, const double* __restrict__ rho,
-                                         double* __restrict__ out, int eb, double* sm) {
+                                         double* __restrict__ out, double* __restrict__ drho,
+                                         int eb, double* sm) {
   constexpr int D = L::D, NL = ipow(NP, D), NT = EPB * NL;
   const int64_t V = v.V;
   const int E = v.E;
@@ -271,6 +296,10 @@ __device__ __forceinline__ void body_lap(const View& v, const double* __restrict
     load_rows<D, NP>(sD, ix, false, Dr);
     double g[D];
     grad_ref<D, NP>(Dr, ix, sr + le * NL, k, g);
+    if (drho) {   // reused by k_force and k_rhs of the same stage
+#pragma unroll
+      for (int b = 0; b < D; ++b) drho[b * V + idx] = g[b];
+    }
     if constexpr (D == 2) {
       const double g00 = __ldg(Gm + idx), g01 = __ldg(Gm + V + idx), g11 = __ldg(Gm + 2 * V + idx);
       st[tid] = fma(g01, g[1], g00 * g[0]);
@@ -349,7 +378,8 @@ __device__ __forceinline__ void body_force(const View& v, int eb, double* sm) {
     double Dr[D][NP];
     load_rows<D, NP>(sD, ix, false, Dr);
     double dr[D], dm[D];
-    grad_ref<D, NP>(Dr, ix, sr + le * NL, k, dr);
+#pragma unroll
+    for (int b = 0; b < D; ++b) dr[b] = v.drho[b * V + idx];
     grad_ref<D, NP>(Dr, ix, smu + le * NL, k, dm);
     const double rh = sr[le * NL + k];
     const double me = __ldg(Me + idx);
@@ -383,7 +413,7 @@ __device__ __forceinline__ void body_dss_collide(const View& v, int g) {
   const int j0 = off[g], j1 = off[g + 1];
   const int i0 = idx[j0];
   const double im = __ldg(v.invMg + g);
-  double F[D];
+  double F[D];   // gather-scatter average of M_e F_e
 #pragma unroll
   for (int a = 0; a < D; ++a) {
     double s = Fp[a * V + i0];
@@ -420,22 +450,28 @@ __device__ __forceinline__ void body_dss_collide(const View& v, int g) {
     uF = fma(u[a], F[a], uF);
   }
   const double base_eq = fma(-1.5, uu, 1.0);   // 1 - u^2/(2 c_s^2)
-  const double hdt = 0.5 * dt;
-  auto relax = [&](double fv, double t, double eu, double eF) {
-    // f^eq (Eq. geq_s) and F** (Sec. 2.1) with c_s^2 = 1/3
-    const double feq = rh * t * fma(eu, fma(4.5, eu, 3.0), base_eq);
-    const double fss = 3.0 * t * fma(3.0 * eu, eF, -uF);
-    const double fbeq = fma(-hdt, fss, feq);
-    return fma(dt, fss, fma(-omega, fv - fbeq, fv));
-  };
+  // f* = fbar - omega (fbar - f^eq + dt F**/2) + dt F**
+  //    = (1 - omega) fbar + omega f^eq + dt (1 - omega/2) F**,
+  // f^eq = rho t (1 + 3 e.u + 4.5 (e.u)^2 - 1.5 u^2)   (Eq. geq_s, c_s^2 = 1/3)
+  // F**  = 3 t (3 (e.u)(e.F) - u.F)                      (Sec. 2.1)
+  const double a = 1.0 - omega;
+  const double wr = omega * rh;
+  const double bdt = dt * (1.0 - 0.5 * omega);
   double out[Q];
-  out[0] = relax(fa[0], L::t(0), 0.0, 0.0);
+  {
+    constexpr double T0 = L::t(0);
+    out[0] = fma(a, fa[0], fma(wr * T0, base_eq, (3.0 * T0 * bdt) * -uF));
+  }
   static_for<0, L::NREP>([&](auto R) {
     constexpr int A = L::rep(decltype(R)::value), B = L::opp(A);
-    const double eu = L::S * L::template cdot<A>(u);
-    const double eF = L::S * L::template cdot<A>(F);
-    out[A] = relax(fa[A], L::t(A), eu, eF);
-    out[B] = relax(fa[B], L::t(A), -eu, -eF);
+    constexpr double T = L::t(A);
+    const double cu = L::template cdot<A>(u);
+    const double cF = L::template cdot<A>(F);
+    const double eu = L::S * cu;
+    const double fss = (3.0 * T * bdt) * fma(3.0 * L::S * L::S, cu * cF, -uF);  // same for A and B
+    const double wrt = wr * T;
+    out[A] = fma(a, fa[A], fma(wrt, fma(eu, fma(4.5, eu, 3.0), base_eq), fss));
+    out[B] = fma(a, fa[B], fma(wrt, fma(-eu, fma(-4.5, eu, 3.0), base_eq), fss));
   });
   for (int j = j0; j < j1; ++j) {
     const int ii = idx[j];
@@ -481,7 +517,8 @@ __device__ __forceinline__ void body_rhs(const View& v, const double* __restrict
   double Dr[D][NP];
   load_rows<D, NP>(sD, ix, false, Dr);
   double dr[D], dm[D];
-  grad_ref<D, NP>(Dr, ix, sr + lb, k, dr);
+#pragma unroll
+  for (int b = 0; b < D; ++b) dr[b] = v.drho[b * V + idx];
   grad_ref<D, NP>(Dr, ix, smu + lb, k, dm);
   const double rh3 = kInvCs2 * sr[lb + k];
   double vv[D];   // d_b rho - (rho / c_s^2) d_b mu, reference components
@@ -500,17 +537,17 @@ __device__ __forceinline__ void body_rhs(const View& v, const double* __restrict
     double c[D];   // (J^-1 C_A)_b: e_A . grad = S sum_b c_b d_b
 #pragma unroll
     for (int b = 0; b < D; ++b) c[b] = L::template cdot<A>(J[b]);
-    double dg[D];
-    grad_ref<D, NP>(Dr, ix, sg + (A - 1) * NT + lb, k, dg);
-    double s = c[0] * fma(T, vv[0], -dg[0]);
+    double dA[D], dB[D];
+    grad_ref2<D, NP>(Dr, ix, sg + (A - 1) * NT + lb, sg + (B - 1) * NT + lb, k, dA, dB);
+    double sA = c[0] * fma(T, vv[0], -dA[0]);
+    double sB = c[0] * fma(T, vv[0], -dB[0]);
 #pragma unroll
-    for (int b = 1; b < D; ++b) s = fma(c[b], fma(T, vv[b], -dg[b]), s);
-    double rA = ms * s;
-    grad_ref<D, NP>(Dr, ix, sg + (B - 1) * NT + lb, k, dg);
-    s = c[0] * fma(T, vv[0], -dg[0]);
-#pragma unroll
-    for (int b = 1; b < D; ++b) s = fma(c[b], fma(T, vv[b], -dg[b]), s);
-    double rB = -ms * s;
+    for (int b = 1; b < D; ++b) {
+      sA = fma(c[b], fma(T, vv[b], -dA[b]), sA);
+      sB = fma(c[b], fma(T, vv[b], -dB[b]), sB);
+    }
+    double rA = ms * sA;
+    double rB = -ms * sB;
     if (slot >= 0) {
       const double gA = sg[(A - 1) * NT + lb + k], gB = sg[(B - 1) * NT + lb + k];
       rA = fma(__ldg(wae + (int64_t)A * R + slot), gA - gB, rA);
@@ -539,24 +576,26 @@ __device__ __forceinline__ void body_dss_rk(const View& v, const double* __restr
   const int j0 = off[g], j1 = off[g + 1];
   const int i0 = idx[j0];
   const double im = __ldg(v.invMg + g);
+  const double imdt = im * dt;   // dt L = dt DSS(r) / M_g
   double val[Q];
   double rs = 0.0;
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
-    double Lq = 0.0;
+    double sq = 0.0;   // DSS(r_q); the rest population does not stream
     if (q > 0) {
-      double s = r[q * V + i0];
-      for (int j = j0 + 1; j < j1; ++j) s += r[q * V + idx[j]];
-      Lq = s * im;
+      sq = r[q * V + i0];
+      for (int j = j0 + 1; j < j1; ++j) sq += r[q * V + idx[j]];
     }
     const double u0 = U0[q * V + i0];
     double x;
     if constexpr (STAGE == 1) {
-      x = fma(dt, Lq, u0);
+      x = (q > 0) ? fma(sq, imdt, u0) : u0;
     } else if constexpr (STAGE == 2) {
-      x = fma(0.25, fma(dt, Lq, gcur[q * V + i0]), 0.75 * u0);
+      const double base = fma(0.25, gcur[q * V + i0], 0.75 * u0);
+      x = (q > 0) ? fma(sq, 0.25 * imdt, base) : base;
     } else {
-      x = fma(2.0 / 3.0, fma(dt, Lq, gcur[q * V + i0]), u0 * (1.0 / 3.0));
+      const double base = fma(2.0 / 3.0, gcur[q * V + i0], u0 * (1.0 / 3.0));
+      x = (q > 0) ? fma(sq, (2.0 / 3.0) * imdt, base) : base;
     }
     val[q] = x;
     rs += x;
@@ -570,14 +609,22 @@ __device__ __forceinline__ void body_dss_rk(const View& v, const double* __restr
   }
 }
 
+// resident CTAs per SM the streaming kernel is compiled for (register cap)
+// (three CTAs of up to 256 threads; larger tiles keep the compiler's choice)
+template <int D, int NP, int EPB>
+constexpr int rhs_min_blocks() {
+  return cta_threads<D, NP, EPB>() <= 256 ? 3 : 1;
+}
+
 // ---------------------------------------------------------------------------
 // single-solve kernels: one CTA per element batch / one thread per node group
 // ---------------------------------------------------------------------------
 template <class L, int NP, int EPB>
 __global__ void __launch_bounds__(cta_threads<L::D, NP, EPB>())
-    k_lap(View v, const double* __restrict__ rho, double* __restrict__ out) {
+    k_lap(View v, const double* __restrict__ rho, double* __restrict__ out,
+          double* __restrict__ drho) {
   extern __shared__ double sm[];
-  body_lap<L, NP, EPB>(v, rho, out, blockIdx.x, sm);
+  body_lap<L, NP, EPB>(v, rho, out, drho, blockIdx.x, sm);
 }
 
 static __global__ void k_dss_mu(View v, const double* __restrict__ lapr, const double* __restrict__ rho,
@@ -597,7 +644,7 @@ __global__ void k_dss_collide(View v) {
 }
 
 template <class L, int NP, int EPB>
-__global__ void __launch_bounds__(cta_threads<L::D, NP, EPB>())
+__global__ void __launch_bounds__(cta_threads<L::D, NP, EPB>(), rhs_min_blocks<L::D, NP, EPB>())
     k_rhs(View v, const double* __restrict__ gst) {
   extern __shared__ double sm[];
   body_rhs<L, NP, EPB>(v, gst, blockIdx.x, sm);
@@ -627,7 +674,7 @@ __global__ void __launch_bounds__(cta_threads<L::D, NP, EPB>())
   for (int w = blockIdx.x; w < n; w += gridDim.x) {
     const WorkItem it = items[w];
     const View& v = slots[it.slot];
-    body_lap<L, NP, EPB>(v, v.rho, v.lapr, it.unit, sm);
+    body_lap<L, NP, EPB>(v, v.rho, v.lapr, v.drho, it.unit, sm);
     __syncthreads();
   }
 }
@@ -667,7 +714,7 @@ __global__ void kb_dss_collide(const View* __restrict__ slots, const WorkItem* _
 }
 
 template <class L, int NP, int EPB>
-__global__ void __launch_bounds__(cta_threads<L::D, NP, EPB>())
+__global__ void __launch_bounds__(cta_threads<L::D, NP, EPB>(), rhs_min_blocks<L::D, NP, EPB>())
     kb_rhs(const View* __restrict__ slots, const WorkItem* __restrict__ items,
            const int* __restrict__ count, int from_fs) {
   extern __shared__ double sm[];

@@ -255,7 +255,7 @@ struct Impl {
         std::sqrt(2.0 * s.beta / s.kappa), s.wet, s.ae);
   }
   static void lap(sem_lbm& s) {
-    k_lap<L, NP, EPB><<<blocks(s), THREADS, SM_LAP, s.stream>>>(s.view, s.rho, s.lapr);
+    k_lap<L, NP, EPB><<<blocks(s), THREADS, SM_LAP, s.stream>>>(s.view, s.rho, s.lapr, s.drho);
   }
   static void mu(sem_lbm& s) {
     k_dss_mu<<<grid_of(s.G, kDssThreads), kDssThreads, 0, s.stream>>>(s.view, s.lapr, s.rho, s.mu);
@@ -292,7 +292,7 @@ struct Impl {
     k_velocity<L><<<grid_of(s.V, 256), 256, 0, s.stream>>>(s.f, u, s.V);
   }
   static void lap_into(sem_lbm& s, const double* rho_in, double* partial) {
-    k_lap<L, NP, EPB><<<blocks(s), THREADS, SM_LAP, s.stream>>>(s.view, rho_in, partial);
+    k_lap<L, NP, EPB><<<blocks(s), THREADS, SM_LAP, s.stream>>>(s.view, rho_in, partial, nullptr);
   }
   static void mu_from(sem_lbm& s, const double* partial, const double* rho_in, double* mu_out) {
     k_dss_mu<<<grid_of(s.G, kDssThreads), kDssThreads, 0, s.stream>>>(s.view, partial, rho_in,
@@ -370,6 +370,7 @@ size_t layout(sem_lbm& s, char* base) {
   s.mu = c.take<double>(V);
   s.lapr = c.take<double>(V);
   s.Fp = c.take<double>(D * V);
+  s.drho = c.take<double>(D * V);
   s.Jinv = c.take<double>(D * D * V);
   s.Gm = c.take<double>(D * (D + 1) / 2 * V);
   s.Me = c.take<double>(V);
@@ -396,7 +397,7 @@ size_t layout(sem_lbm& s, char* base) {
 void fill_view(sem_lbm& s) {
   View& v = s.view;
   v.f = s.f; v.fs = s.fs; v.g = s.g; v.r = s.r;
-  v.rho = s.rho; v.mu = s.mu; v.lapr = s.lapr; v.Fp = s.Fp;
+  v.rho = s.rho; v.mu = s.mu; v.lapr = s.lapr; v.Fp = s.Fp; v.drho = s.drho;
   v.flags = s.flags;
   v.Jinv = s.Jinv; v.Gm = s.Gm; v.Me = s.Me; v.invMg = s.invMg; v.Dm = s.Dm;
   v.off = s.off; v.idx = s.idx; v.wslot = s.slot; v.wet = s.wet; v.ae = s.ae;

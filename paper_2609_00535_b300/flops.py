@@ -6,7 +6,8 @@ the method, not the instructions a compiler emits): a fused multiply-add is
 n = N+1, d the dimension, M = Q-1 moving velocities.
 
 k_rhs (force-split streaming right-hand side, per element-local node):
-  reference derivatives of rho and mu       2d derivatives
+  reference derivatives of mu               d derivatives (those of rho are
+                                            stored by k_lap of the same stage)
   v_b = d_b rho - (rho/c_s^2) d_b mu        1 mul + d fma
   M_e * |e| scale                           1 mul
   per velocity pair, c = J^-1 C_alpha       D2Q9: 0 (axis) or d adds (diagonal);
@@ -27,8 +28,8 @@ def rhs_work_per_node(lattice, N):
     Q = 9 if lattice == "D2Q9" else 13
     M = Q - 1
     dv = _deriv(n)
-    ops = 2 * d * dv["ops"] + 1 + d + 1
-    flops = 2 * d * dv["flops"] + 1 + 2 * d + 1
+    ops = d * dv["ops"] + 1 + d + 1
+    flops = d * dv["flops"] + 1 + 2 * d + 1
     if lattice == "D2Q9":
         ops += 2 * d            # two diagonal pairs: d adds each
         flops += 2 * d
@@ -49,8 +50,8 @@ def rhs_work(lattice, N, n_local, n_wall_nodes):
 
 
 def rhs_bytes_per_node(lattice, N):
-    """Minimum DRAM bytes of k_rhs per node: read g (Q-1), rho, mu, J^-1 (d^2),
-    M_e, wall slot (4 B); write r (Q-1)."""
+    """Minimum DRAM bytes of k_rhs per node: read g (Q-1), rho, mu, grad rho (d),
+    J^-1 (d^2), M_e, wall slot (4 B); write r (Q-1)."""
     d = 2 if lattice == "D2Q9" else 3
     Q = 9 if lattice == "D2Q9" else 13
-    return 8 * ((Q - 1) + 2 + d * d + 1 + (Q - 1)) + 4
+    return 8 * ((Q - 1) + 2 + d + d * d + 1 + (Q - 1)) + 4
