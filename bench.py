@@ -378,6 +378,8 @@ def native_arm(args):
                          "fp64_op_frac": work["ops"] / (rhs_ms * 1e-3) / (peak * 1e12 / 2),
                          "kernel_ms": rhs_ms, "flops_per_launch": work["flops"]},
             "kernel_share": shares,
+            "kernel_ms_per_launch": {k: round(prof["ms"][k] / max(1, prof["launches"][k]), 4)
+                                     for k in prof["ms"]},
             "gpu_launches": int(sum(prof["launches"].values())),
             "clocks": clk,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": Q * V * 8,

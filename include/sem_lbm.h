@@ -29,7 +29,11 @@
  *     D3Q13: 0 rest, then s*(0,1,phi), s*(0,-1,phi), s*(1,phi,0),
  *     s*(-1,phi,0), s*(phi,0,1), s*(phi,0,-1) and e_{a+6} = -e_a, with
  *     phi the golden ratio and |e| = sqrt(5/3); weights 2/5 and 1/20.
- *     c_s^2 = 1/3 for both.
+ *     D3Q19: 0 rest, 1-3 (1,0,0) (0,1,0) (0,0,1), 4-9 (1,1,0) (1,-1,0) (1,0,1)
+ *     (1,0,-1) (0,1,1) (0,1,-1), e_{a+9} = -e_a; weights 1/3, 1/18, 1/36.
+ *     D3Q27: as D3Q19 for 1-9, then 10-13 (1,1,1) (1,1,-1) (1,-1,1) (1,-1,-1),
+ *     e_{a+13} = -e_a; weights 8/27, 2/27, 1/54, 1/216.
+ *     c_s^2 = 1/3 for all.
  *   - Calls on one solver are not thread safe; distinct solvers are
  *     independent.  Work is enqueued on the solver's stream (params.stream,
  *     else a stream the solver owns).
@@ -54,7 +58,12 @@ enum {
   SEMLBM_EUNSUPPORTED = -6 /* order N or lattice/dimension pair not built       */
 };
 
-typedef enum { SEMLBM_D2Q9 = 0, SEMLBM_D3Q13 = 1 } sem_lbm_lattice;
+typedef enum {
+  SEMLBM_D2Q9 = 0,   /* 2D, Sec. 2.1                                        */
+  SEMLBM_D3Q13 = 1,  /* 3D, Sec. 3.2 (rest + icosahedron)                   */
+  SEMLBM_D3Q19 = 2,  /* 3D cubic, faces + edges                             */
+  SEMLBM_D3Q27 = 3   /* 3D cubic, faces + edges + corners                   */
+} sem_lbm_lattice;
 
 /* Mesh (host memory; copied by sem_lbm_create, the caller keeps ownership).
  *   node_xyz  [n_elem][(N+1)^dim][dim]  GLL node coordinates of each element
@@ -121,7 +130,7 @@ size_t sem_lbm_workspace_bytes(const sem_lbm_mesh* mesh, int N, sem_lbm_lattice 
 /* Build a solver: validates the mesh, builds GLL tables, the gather-scatter
  * map and the wall records on the host, uploads the mesh and computes the
  * geometry (Jacobians, metrics, masses, wall area vectors) in kernels.
- *   N        polynomial order: 2..16 for D2Q9, 2..8 for D3Q13
+ *   N        polynomial order: 2..16 for D2Q9, 2..8 for the 3D sets
  *   beta     bulk free-energy coefficient of e0 = beta (rho-rl)^2 (rho-rv)^2
  *   kappa    gradient-energy coefficient (Appendix A: beta delta^2 (rl-rv)^2/8)
  *   tau      relaxation time in units of dt; collision rate 1/(tau + 1/2)
@@ -218,6 +227,7 @@ typedef struct {
   int lattice, N, n_members, epb;     /* epb: elements per CTA in use          */
   int64_t elem_items, node_items;     /* work-list lengths                      */
   int grid_elem, grid_node;           /* persistent grid sizes                  */
+  int capture_failures;               /* batch steps run as direct launches     */
   int n_candidates;                   /* tile shapes the tuner can choose from  */
   int candidate_epb[4];
   double candidate_ms[4];             /* measured ms per step (0 until tuned)   */

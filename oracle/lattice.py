@@ -1,6 +1,7 @@
 """Discrete velocity sets for the oracle (test infrastructure only).
 
 * D2Q9, the 2D set of Sec. 2.1 (standard weights 4/9, 1/9, 1/36; c_s^2 = 1/3).
+* D3Q19 and D3Q27, the standard cubic 3D sets (alternatives to D3Q13).
 * D3Q13 for the 3D case of Sec. 3.2.  The paper cites Shan (2006) without a
   table.  Reading used here: the rest velocity plus the 12 vertices of an
   icosahedron, |e| = sqrt(5 c_s^2), weights 2/5 and 1/20, c_s^2 = 1/3.  That is
@@ -51,5 +52,29 @@ def d3q13():
     return Lattice("D3Q13", e, t)
 
 
+_FACES = [(1, 0, 0), (0, 1, 0), (0, 0, 1)]
+_EDGES = [(1, 1, 0), (1, -1, 0), (1, 0, 1), (1, 0, -1), (0, 1, 1), (0, 1, -1)]
+_CORNERS = [(1, 1, 1), (1, 1, -1), (1, -1, 1), (1, -1, -1)]
+
+
+def _paired(half, weights, t0):
+    half = np.array(half, dtype=np.float64)
+    e = np.vstack([np.zeros((1, 3)), half, -half])
+    t = np.array([t0] + list(weights) + list(weights))
+    return e, t
+
+
+def d3q19():
+    """Rest, 6 face and 12 edge neighbours (weights 1/3, 1/18, 1/36); e_{a+9} = -e_a."""
+    e, t = _paired(_FACES + _EDGES, [1 / 18] * 3 + [1 / 36] * 6, 1 / 3)
+    return Lattice("D3Q19", e, t)
+
+
+def d3q27():
+    """Rest, faces, edges and corners (8/27, 2/27, 1/54, 1/216); e_{a+13} = -e_a."""
+    e, t = _paired(_FACES + _EDGES + _CORNERS, [2 / 27] * 3 + [1 / 54] * 6 + [1 / 216] * 4, 8 / 27)
+    return Lattice("D3Q27", e, t)
+
+
 def by_name(name):
-    return {"D2Q9": d2q9, "D3Q13": d3q13}[name]()
+    return {"D2Q9": d2q9, "D3Q13": d3q13, "D3Q19": d3q19, "D3Q27": d3q27}[name]()

@@ -128,8 +128,13 @@ std::vector<GroupOps> pick_candidates(int N, int sms, std::integer_sequence<int,
 constexpr int kBatchMaxN = 8;   // batched kernels are compiled for N = 2..8
 
 std::vector<GroupOps> group_candidates(sem_lbm_lattice lat, int N, int sms) {
-  if (lat == SEMLBM_D2Q9) return pick_candidates<D2Q9>(N, sms, std::make_integer_sequence<int, 7>{});
-  return pick_candidates<D3Q13>(N, sms, std::make_integer_sequence<int, 7>{});
+  switch (lat) {
+    case SEMLBM_D2Q9: return pick_candidates<D2Q9>(N, sms, std::make_integer_sequence<int, 7>{});
+    case SEMLBM_D3Q13: return pick_candidates<D3Q13>(N, sms, std::make_integer_sequence<int, 7>{});
+    case SEMLBM_D3Q19: return pick_candidates<D3Q19>(N, sms, std::make_integer_sequence<int, 7>{});
+    case SEMLBM_D3Q27: return pick_candidates<D3Q27>(N, sms, std::make_integer_sequence<int, 7>{});
+  }
+  return {};
 }
 
 // tuned choices of this process: (lattice, N, log2 of the group's element count) -> EPB
@@ -173,6 +178,7 @@ struct sem_lbm_batch {
   bool dirty = true;
   cudaGraphExec_t graph = nullptr;
   cudaEvent_t fork = nullptr;
+  int capture_failures = 0;   // steps that ran as direct launches instead
 };
 
 namespace {
@@ -253,7 +259,9 @@ int capture(sem_lbm_batch* b) {
     b->graph = nullptr;
   }
   cudaGraph_t gr;
-  CUDA_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+  // relaxed: other host threads (e.g. a server building the next solves) may
+  // allocate or launch on their own streams meanwhile
+  CUDA_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeRelaxed));
   cudaError_t e = cudaEventRecord(b->fork, b->stream);
   for (BatchGroup* g : b->groups) {
     if (e == cudaSuccess) e = cudaStreamWaitEvent(g->branch, b->fork, 0);
@@ -395,8 +403,20 @@ int sem_lbm_batch_step(sem_lbm_batch_t* b, int64_t n_steps) {
   if (!b) return fail(SEMLBM_EINVAL, "NULL batch");
   if (n_steps < 0) return fail(SEMLBM_EINVAL, "n_steps must be >= 0");
   if (b->groups.empty() || n_steps == 0) return 0;
-  if (b->dirty || !b->graph)
-    if (int rc = capture(b)) return rc;
+  if (b->dirty || !b->graph) {
+    if (capture(b) != 0) {
+      // a capture that failed leaves no graph: run these steps as direct
+      // launches of the same kernels (same results) and capture next time
+      cudaGetLastError();
+      ++b->capture_failures;
+      for (int64_t i = 0; i < n_steps; ++i)
+        for (BatchGroup* g : b->groups) g->cands[g->choice].step(g->cands[g->choice], dev_of(g), b->stream);
+      CUDA_TRY(cudaGetLastError());
+      for (sem_lbm* s : b->slots)
+        if (s) s->step += n_steps;
+      return 0;
+    }
+  }
   for (int64_t i = 0; i < n_steps; ++i) CUDA_TRY(cudaGraphLaunch(b->graph, b->stream));
   for (sem_lbm* s : b->slots)
     if (s) s->step += n_steps;
@@ -500,6 +520,7 @@ int sem_lbm_batch_info(sem_lbm_batch_t* b, sem_lbm_batch_group_info* out, int ma
     o.node_items = g->h_counts[1];
     o.grid_elem = g->cands[g->choice].grid_rhs;
     o.grid_node = g->cands[g->choice].grid_node;
+    o.capture_failures = b->capture_failures;
     o.n_candidates = (int)std::min<size_t>(g->cands.size(), 4);
     for (int c = 0; c < o.n_candidates; ++c) {
       o.candidate_epb[c] = g->cands[c].epb;

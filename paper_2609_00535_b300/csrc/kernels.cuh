@@ -558,12 +558,30 @@ __device__ __forceinline__ void body_rhs(const View& v, const double* __restrict
   });
 }
 
+// SSP-RK3 stage value from the base state u0, the current stage state gc and
+// sq = DSS(r_q) (imdt = dt / M_g); the rest population (q = 0) has L = 0
+template <int STAGE>
+__device__ __forceinline__ double rk_update(int q, double sq, double imdt, double u0, double gc) {
+  if constexpr (STAGE == 1) {
+    return (q > 0) ? fma(sq, imdt, u0) : u0;
+  } else if constexpr (STAGE == 2) {
+    const double base = fma(0.25, gc, 0.75 * u0);
+    return (q > 0) ? fma(sq, 0.25 * imdt, base) : base;
+  } else {
+    const double base = fma(2.0 / 3.0, gc, u0 * (1.0 / 3.0));
+    return (q > 0) ? fma(sq, (2.0 / 3.0) * imdt, base) : base;
+  }
+}
+
 // a5 (part 2): DSS of the right-hand side, M^-1, and the SSP-RK3 stage update
 //   stage 1: U1 = U0 + dt L;  stage 2: U2 = 3/4 U0 + 1/4 (U1 + dt L);
 //   stage 3: f^{n+1} = 1/3 U0 + 2/3 (U2 + dt L); rho of the new state
+// gcur and out may be the same array (stage 2 updates the stage state in
+// place): each group reads all its values before writing any, so the pointers
+// are deliberately not restrict-qualified
 template <class L, int STAGE>
-__device__ __forceinline__ void body_dss_rk(const View& v, const double* __restrict__ gcur,
-                                            double* __restrict__ out, int g) {
+__device__ __forceinline__ void body_dss_rk(const View& v, const double* gcur, double* out,
+                                            int g) {
   constexpr int Q = L::Q;
   if (g >= v.G) return;
   const int64_t V = v.V;
@@ -572,11 +590,9 @@ __device__ __forceinline__ void body_dss_rk(const View& v, const double* __restr
   const double* __restrict__ r = v.r;
   const double* __restrict__ U0 = v.fs;
   double* __restrict__ rho = v.rho;
-  const double dt = v.dt;
   const int j0 = off[g], j1 = off[g + 1];
   const int i0 = idx[j0];
-  const double im = __ldg(v.invMg + g);
-  const double imdt = im * dt;   // dt L = dt DSS(r) / M_g
+  const double imdt = __ldg(v.invMg + g) * v.dt;   // dt L = dt DSS(r) / M_g
   double val[Q];
   double rs = 0.0;
 #pragma unroll
@@ -586,19 +602,8 @@ __device__ __forceinline__ void body_dss_rk(const View& v, const double* __restr
       sq = r[q * V + i0];
       for (int j = j0 + 1; j < j1; ++j) sq += r[q * V + idx[j]];
     }
-    const double u0 = U0[q * V + i0];
-    double x;
-    if constexpr (STAGE == 1) {
-      x = (q > 0) ? fma(sq, imdt, u0) : u0;
-    } else if constexpr (STAGE == 2) {
-      const double base = fma(0.25, gcur[q * V + i0], 0.75 * u0);
-      x = (q > 0) ? fma(sq, 0.25 * imdt, base) : base;
-    } else {
-      const double base = fma(2.0 / 3.0, gcur[q * V + i0], u0 * (1.0 / 3.0));
-      x = (q > 0) ? fma(sq, (2.0 / 3.0) * imdt, base) : base;
-    }
-    val[q] = x;
-    rs += x;
+    val[q] = rk_update<STAGE>(q, sq, imdt, U0[q * V + i0], gcur[q * V + i0]);
+    rs += val[q];
   }
   if (nonfinite(rs)) atomicOr(v.flags + 1, 1);
   for (int j = j0; j < j1; ++j) {
@@ -651,7 +656,7 @@ __global__ void __launch_bounds__(cta_threads<L::D, NP, EPB>(), rhs_min_blocks<L
 }
 
 template <class L, int STAGE>
-__global__ void k_dss_rk(View v, const double* __restrict__ gcur, double* __restrict__ out) {
+__global__ void k_dss_rk(View v, const double* gcur, double* out) {
   body_dss_rk<L, STAGE>(v, gcur, out, blockIdx.x * blockDim.x + threadIdx.x);
 }
 

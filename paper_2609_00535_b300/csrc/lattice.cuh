@@ -1,5 +1,6 @@
 // Velocity sets as compile-time structure (Sec. 2.1: D2Q9; Sec. 3.2: a
-// 13-velocity 3D set, read as rest + icosahedron vertices, |e| = sqrt(5/3)).
+// 13-velocity 3D set, read as rest + icosahedron vertices, |e| = sqrt(5/3);
+// the cubic D3Q19 and D3Q27 as alternatives).
 //
 // Velocities are e_a = S * C_a with C_a built from 0, +-1 and +-phi, ordered
 // so that a's opposite is known at compile time.  The helpers below contract
@@ -62,6 +63,60 @@ struct D3Q13 {
     else return fma(kPhi, v[0], -v[2]);              // A == 6
   }
 };
+
+// C . v for an integer velocity C with components in {-1, 0, 1} and a positive
+// first non-zero component (the representatives of the cubic sets below)
+template <int C0, int C1, int C2>
+__device__ __forceinline__ double idot3(const double* v) {
+  double r;
+  if constexpr (C0 != 0) {
+    r = v[0];
+    if constexpr (C1 > 0) r += v[1];
+    else if constexpr (C1 < 0) r -= v[1];
+    if constexpr (C2 > 0) r += v[2];
+    else if constexpr (C2 < 0) r -= v[2];
+  } else if constexpr (C1 != 0) {
+    r = v[1];
+    if constexpr (C2 > 0) r += v[2];
+    else if constexpr (C2 < 0) r -= v[2];
+  } else {
+    r = v[2];
+  }
+  return r;
+}
+
+// representatives of the cubic sets: faces, edges, corners
+__host__ __device__ constexpr int cubic_rep(int r, int c) {
+  constexpr int tab[13][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1},  {1, 1, 0},  {1, -1, 0},
+                              {1, 0, 1}, {1, 0, -1}, {0, 1, 1}, {0, 1, -1}, {1, 1, 1},
+                              {1, 1, -1}, {1, -1, 1}, {1, -1, -1}};
+  return tab[r][c];
+}
+
+// D3Q19 and D3Q27: cubic velocity sets (c_s^2 = 1/3), e_{a+H} = -e_a
+template <int NR>
+struct Cubic {
+  static constexpr int D = 3, Q = 2 * NR + 1, NREP = NR;
+  static constexpr double S = 1.0;
+  static constexpr double SPEED_MAX = (NR == 9) ? 1.4142135623730951 : 1.7320508075688772;
+  __host__ __device__ static constexpr int rep(int r) { return 1 + r; }
+  __host__ __device__ static constexpr int opp(int a) { return a == 0 ? 0 : (a <= NR ? a + NR : a - NR); }
+  __host__ __device__ static constexpr double t(int a) {
+    return NR == 9 ? (a == 0 ? 1.0 / 3.0 : (((a - 1) % 9) < 3 ? 1.0 / 18.0 : 1.0 / 36.0))
+                   : (a == 0 ? 8.0 / 27.0
+                             : (((a - 1) % 13) < 3 ? 2.0 / 27.0
+                                                   : (((a - 1) % 13) < 9 ? 1.0 / 54.0 : 1.0 / 216.0)));
+  }
+  __host__ __device__ static constexpr double C(int a, int c) {
+    return a == 0 ? 0.0 : (a <= NR ? cubic_rep(a - 1, c) : -cubic_rep(a - 1 - NR, c));
+  }
+  template <int A>
+  __device__ static __forceinline__ double cdot(const double* v) {
+    return idot3<cubic_rep(A - 1, 0), cubic_rep(A - 1, 1), cubic_rep(A - 1, 2)>(v);
+  }
+};
+using D3Q19 = Cubic<9>;
+using D3Q27 = Cubic<13>;
 
 // compile-time loop: f(std::integral_constant<int, I>) for I in [B, E)
 template <int I> struct Int { static constexpr int value = I; };

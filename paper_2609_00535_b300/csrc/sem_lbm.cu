@@ -10,6 +10,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <tuple>
 #include <utility>
 #include <vector>
 
@@ -102,7 +103,9 @@ int build_maps(const sem_lbm_mesh* m, int N, double theta_w, const sem_lbm_param
   std::vector<std::pair<int64_t, int>> key(V);
   for (int64_t i = 0; i < V; ++i) key[i] = {m->global_id[i], (int)i};
   std::sort(key.begin(), key.end());
-  std::vector<std::pair<int, int>> grp;   // (first local index, start in key)
+  // groups ordered by their first copy, so that consecutive gather-scatter
+  // threads touch nearby memory
+  std::vector<std::tuple<int, int>> grp;   // (first local index, start in key)
   for (int64_t i = 0; i < V; ++i)
     if (i == 0 || key[i].first != key[i - 1].first) grp.push_back({key[i].second, (int)i});
   std::sort(grp.begin(), grp.end());
@@ -112,7 +115,8 @@ int build_maps(const sem_lbm_mesh* m, int N, double theta_w, const sem_lbm_param
   int pos = 0;
   for (int64_t g = 0; g < h.G; ++g) {
     h.off[g] = pos;
-    for (int64_t i = grp[g].second; i < V && key[i].first == key[grp[g].second].first; ++i)
+    const int start = std::get<1>(grp[g]);
+    for (int64_t i = start; i < V && key[i].first == key[start].first; ++i)
       h.idx[pos++] = key[i].second;
   }
   h.off[h.G] = pos;
@@ -183,12 +187,32 @@ double min_spacing(const sem_lbm_mesh* m, int N) {
   return std::sqrt(h2);
 }
 
+int q_of(sem_lbm_lattice lat) {
+  switch (lat) {
+    case SEMLBM_D2Q9: return 9;
+    case SEMLBM_D3Q13: return 13;
+    case SEMLBM_D3Q19: return 19;
+    case SEMLBM_D3Q27: return 27;
+  }
+  return 0;
+}
+
+double speed_max(sem_lbm_lattice lat) {
+  switch (lat) {
+    case SEMLBM_D2Q9: return D2Q9::SPEED_MAX;
+    case SEMLBM_D3Q13: return D3Q13::SPEED_MAX;
+    case SEMLBM_D3Q19: return D3Q19::SPEED_MAX;
+    case SEMLBM_D3Q27: return D3Q27::SPEED_MAX;
+  }
+  return 1.0;
+}
+
 int validate(const sem_lbm_mesh* m, int N, sem_lbm_lattice lat) {
   if (!m) return fail(SEMLBM_EINVAL, "mesh is NULL");
   if (m->dim != 2 && m->dim != 3) return fail(SEMLBM_EINVAL, "dim must be 2 or 3");
-  if ((lat == SEMLBM_D2Q9 && m->dim != 2) || (lat == SEMLBM_D3Q13 && m->dim != 3))
+  if (q_of(lat) == 0) return fail(SEMLBM_EUNSUPPORTED, "unknown lattice %d", (int)lat);
+  if ((lat == SEMLBM_D2Q9) != (m->dim == 2))
     return fail(SEMLBM_EINVAL, "lattice does not match the mesh dimension");
-  if (lat != SEMLBM_D2Q9 && lat != SEMLBM_D3Q13) return fail(SEMLBM_EUNSUPPORTED, "unknown lattice");
   const int nmax = (m->dim == 2) ? 16 : 8;
   if (N < 2 || N > nmax) return fail(SEMLBM_EUNSUPPORTED, "N = %d not built (2..%d)", N, nmax);
   if (m->n_elem <= 0) return fail(SEMLBM_EINVAL, "n_elem must be positive");
@@ -313,8 +337,13 @@ Ops* pick(int N, std::integer_sequence<int, Ns...>) {
 }
 
 Ops* select_ops(sem_lbm_lattice lat, int N) {
-  if (lat == SEMLBM_D2Q9) return pick<D2Q9>(N, std::make_integer_sequence<int, 15>{});  // n = 3..17
-  return pick<D3Q13>(N, std::make_integer_sequence<int, 7>{});                          // n = 3..9
+  switch (lat) {
+    case SEMLBM_D2Q9: return pick<D2Q9>(N, std::make_integer_sequence<int, 15>{});   // n = 3..17
+    case SEMLBM_D3Q13: return pick<D3Q13>(N, std::make_integer_sequence<int, 7>{});  // n = 3..9
+    case SEMLBM_D3Q19: return pick<D3Q19>(N, std::make_integer_sequence<int, 7>{});
+    case SEMLBM_D3Q27: return pick<D3Q27>(N, std::make_integer_sequence<int, 7>{});
+  }
+  return nullptr;
 }
 
 enum { K_LAP = 0, K_MU, K_FORCE, K_COLLIDE, K_RHS, K_RK };
@@ -442,7 +471,7 @@ size_t sem_lbm_workspace_bytes(const sem_lbm_mesh* mesh, int N, sem_lbm_lattice 
   s.N = N;
   s.n = N + 1;
   s.NL = ipow(s.n, s.D);
-  s.Q = (lattice == SEMLBM_D2Q9) ? 9 : 13;
+  s.Q = q_of(lattice);
   s.E = mesh->n_elem;
   s.V = s.E * s.NL;
   s.G = h.G;
@@ -472,7 +501,7 @@ int sem_lbm_create(const sem_lbm_mesh* mesh, int N, sem_lbm_lattice lattice, dou
   s->N = N;
   s->n = N + 1;
   s->NL = ipow(s->n, s->D);
-  s->Q = (lattice == SEMLBM_D2Q9) ? 9 : 13;
+  s->Q = q_of(lattice);
   s->E = mesh->n_elem;
   s->V = s->E * s->NL;
   s->G = h.G;
@@ -484,7 +513,7 @@ int sem_lbm_create(const sem_lbm_mesh* mesh, int N, sem_lbm_lattice lattice, dou
   s->rho_l = p.rho_l > 0 ? p.rho_l : 1.0;
   s->rho_v = p.rho_v > 0 ? p.rho_v : 0.1;
   s->mu0f = p.mu0_factor > 0 ? p.mu0_factor : 2.0;
-  const double speed = (lattice == SEMLBM_D2Q9) ? D2Q9::SPEED_MAX : D3Q13::SPEED_MAX;
+  const double speed = speed_max(lattice);
   if (p.dt > 0) {
     s->dt = p.dt;
   } else {

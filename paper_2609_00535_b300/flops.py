@@ -23,19 +23,38 @@ def _deriv(n):
     return {"ops": n, "flops": 2 * n - 1}
 
 
+# non-zero components of each representative velocity (one per opposite pair)
+_REP_NONZERO = {
+    "D2Q9": [1, 1, 2, 2],
+    "D3Q13": [2] * 6,                       # (0, 1, phi) and its cyclic images
+    "D3Q19": [1] * 3 + [2] * 6,
+    "D3Q27": [1] * 3 + [2] * 6 + [3] * 4,
+}
+_DIM = {"D2Q9": 2, "D3Q13": 3, "D3Q19": 3, "D3Q27": 3}
+
+
+def _pair_coeff_work(lattice, d):
+    """c_b = (J^-1 C)_b for every pair: adds for unit components, an fma for phi."""
+    ops = flops = 0
+    for k in _REP_NONZERO[lattice]:
+        if lattice == "D3Q13":
+            ops += d          # one fma per reference direction
+            flops += 2 * d
+        else:
+            ops += (k - 1) * d
+            flops += (k - 1) * d
+    return ops, flops
+
+
 def rhs_work_per_node(lattice, N):
-    n, d = N + 1, (2 if lattice == "D2Q9" else 3)
-    Q = 9 if lattice == "D2Q9" else 13
-    M = Q - 1
+    n, d = N + 1, _DIM[lattice]
+    M = 2 * len(_REP_NONZERO[lattice])   # moving velocities
     dv = _deriv(n)
     ops = d * dv["ops"] + 1 + d + 1
     flops = d * dv["flops"] + 1 + 2 * d + 1
-    if lattice == "D2Q9":
-        ops += 2 * d            # two diagonal pairs: d adds each
-        flops += 2 * d
-    else:
-        ops += 6 * d            # six pairs: d fma each
-        flops += 6 * 2 * d
+    po, pf = _pair_coeff_work(lattice, d)
+    ops += po
+    flops += pf
     per_v_ops = d * dv["ops"] + d + d + 1
     per_v_flops = d * dv["flops"] + 2 * d + (1 + 2 * (d - 1)) + 1
     return {"ops": ops + M * per_v_ops, "flops": flops + M * per_v_flops}
@@ -43,7 +62,7 @@ def rhs_work_per_node(lattice, N):
 
 def rhs_work(lattice, N, n_local, n_wall_nodes):
     """FP64 ops and flops of one k_rhs launch over the whole mesh."""
-    Q = 9 if lattice == "D2Q9" else 13
+    Q = 2 * len(_REP_NONZERO[lattice]) + 1
     w = rhs_work_per_node(lattice, N)
     return {"ops": w["ops"] * n_local + 2 * (Q - 1) * n_wall_nodes,
             "flops": w["flops"] * n_local + 3 * (Q - 1) * n_wall_nodes}
@@ -52,6 +71,6 @@ def rhs_work(lattice, N, n_local, n_wall_nodes):
 def rhs_bytes_per_node(lattice, N):
     """Minimum DRAM bytes of k_rhs per node: read g (Q-1), rho, mu, grad rho (d),
     J^-1 (d^2), M_e, wall slot (4 B); write r (Q-1)."""
-    d = 2 if lattice == "D2Q9" else 3
-    Q = 9 if lattice == "D2Q9" else 13
+    d = _DIM[lattice]
+    Q = 2 * len(_REP_NONZERO[lattice]) + 1
     return 8 * ((Q - 1) + 2 + d + d * d + 1 + (Q - 1)) + 4

@@ -274,7 +274,8 @@ def node_noise(mesh, seed, amplitude):
 # The workloads.  Each returns a Case with everything the library's create()
 # takes plus the initial density and the number of steps.
 # ---------------------------------------------------------------------------
-SPEED_MAX = {"D2Q9": math.sqrt(2.0), "D3Q13": math.sqrt(5.0 / 3.0)}   # max |e_alpha|
+SPEED_MAX = {"D2Q9": math.sqrt(2.0), "D3Q13": math.sqrt(5.0 / 3.0), "D3Q19": math.sqrt(2.0),
+             "D3Q27": math.sqrt(3.0)}   # max |e_alpha|
 
 
 @dataclass
@@ -351,18 +352,18 @@ def cylinder_2d(theta=math.radians(90), N=6, n_theta=64, n_r=16, Rc=0.1, beta=1e
 
 
 def sphere_3d(N=5, ne=(16, 16, 16), theta=math.radians(60), beta=1e-3, Cn=0.08, d=0.25,
-              La=60.0, rho_l=1.0, rho_v=0.1, cfl=0.4, steps=20000):
+              La=60.0, rho_l=1.0, rho_v=0.1, cfl=0.4, steps=20000, lattice="D3Q13"):
     """3D droplet (d = 0.25 at (0.25, 0.25, 0.04)) on a sphere-cap bottom (Sec. 3.2)."""
     mesh = sphere_cap_box(N, ne)
     delta = Cn * d
     kappa = kappa_from_width(beta, delta, rho_l, rho_v)
-    dt = cfl_dt(mesh, "D3Q13", cfl, kappa, rho_l)
+    dt = cfl_dt(mesh, lattice, cfl, kappa, rho_l)
     gamma = (rho_l - rho_v) ** 3 * math.sqrt(2 * kappa * beta) / 6
     eta = math.sqrt(gamma * d / La)          # La = gamma d / eta^2
     nu = eta / rho_l
     tau = nu / ((1.0 / 3.0) * dt)            # nu = tau c_s^2 dt
     rho0 = droplet_density(mesh, (0.25, 0.25, 0.04), d / 2, delta, rho_l, rho_v)
-    return Case("sphere3d", mesh, "D3Q13", rho_l, rho_v, beta, kappa, tau, dt, theta, (),
+    return Case("sphere3d", mesh, lattice, rho_l, rho_v, beta, kappa, tau, dt, theta, (),
                 rho0, steps, {"delta": delta, "La": La})
 
 
@@ -462,3 +463,30 @@ def request_stream(n=500, rate=10.0, seed=5, elems=(256, 8192), orders=(4, 5, 6,
                            math.radians(rng.uniform(15.0, 165.0)), float(rng.uniform(0.8, 1.2)),
                            int(rng.integers(1 << 30))))
     return out
+
+
+# ---------------------------------------------------------------------------
+# Equilibrium-shape initial densities (the paper starts its parasitic-current
+# runs from the equilibrium cap, Sec. 3.1 and Sec. 3.2).
+# ---------------------------------------------------------------------------
+def cap_radius(area, theta):
+    """Radius of a circular cap of the given area meeting a flat wall at theta."""
+    return math.sqrt(area / (theta - math.sin(theta) * math.cos(theta)))
+
+
+def sessile_cap_density(mesh, x_c, area, theta, delta, rho_l=1.0, rho_v=0.1):
+    """Drop on the wall y = 0 at its equilibrium shape: a circle of radius R
+    centred at (x_c, -R cos(theta)) holding `area` above the wall."""
+    R = cap_radius(area, theta)
+    c = np.array([x_c, -R * math.cos(theta)] + [0.0] * (mesh.dim - 2))
+    dist = np.sqrt(((mesh.node_xyz - c) ** 2).sum(-1)) - R
+    return tanh_profile(dist, delta, rho_l, rho_v)
+
+
+def cylinder_cap_density(mesh, center, Rc, Rd, theta, delta, rho_l=1.0, rho_v=0.1):
+    """Drop of radius Rd on a cylinder of radius Rc at its equilibrium position:
+    centre distance d with d^2 = Rc^2 + Rd^2 - 2 Rc Rd cos(theta), along +y."""
+    d = math.sqrt(Rc * Rc + Rd * Rd - 2 * Rc * Rd * math.cos(theta))
+    c = np.asarray(center, dtype=np.float64) + np.array([0.0, d])
+    dist = np.sqrt(((mesh.node_xyz - c) ** 2).sum(-1)) - Rd
+    return tanh_profile(dist, delta, rho_l, rho_v)

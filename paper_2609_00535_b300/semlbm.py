@@ -14,9 +14,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsemlbm.so")
 
-D2Q9, D3Q13 = 0, 1
-LATTICES = {"D2Q9": D2Q9, "D3Q13": D3Q13}
-Q_OF = {D2Q9: 9, D3Q13: 13}
+D2Q9, D3Q13, D3Q19, D3Q27 = 0, 1, 2, 3
+LATTICES = {"D2Q9": D2Q9, "D3Q13": D3Q13, "D3Q19": D3Q19, "D3Q27": D3Q27}
+Q_OF = {D2Q9: 9, D3Q13: 13, D3Q19: 19, D3Q27: 27}
 
 ERRORS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENONFINITE", -5: "ETIMEOUT",
           -6: "EUNSUPPORTED"}
@@ -79,7 +79,8 @@ class GroupInfoC(ctypes.Structure):
     _fields_ = [("lattice", ctypes.c_int), ("N", ctypes.c_int), ("n_members", ctypes.c_int),
                 ("epb", ctypes.c_int), ("elem_items", ctypes.c_int64),
                 ("node_items", ctypes.c_int64), ("grid_elem", ctypes.c_int),
-                ("grid_node", ctypes.c_int), ("n_candidates", ctypes.c_int),
+                ("grid_node", ctypes.c_int), ("capture_failures", ctypes.c_int),
+                ("n_candidates", ctypes.c_int),
                 ("candidate_epb", ctypes.c_int * 4), ("candidate_ms", ctypes.c_double * 4)]
 
 
@@ -348,6 +349,7 @@ class Batch:
             out.append({"lattice": g.lattice, "N": g.N, "n_members": g.n_members, "epb": g.epb,
                         "elem_items": g.elem_items, "node_items": g.node_items,
                         "grid_elem": g.grid_elem, "grid_node": g.grid_node,
+                        "capture_failures": g.capture_failures,
                         "candidates": [(g.candidate_epb[c], g.candidate_ms[c])
                                        for c in range(g.n_candidates)]})
         return out

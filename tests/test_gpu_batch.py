@@ -127,3 +127,19 @@ def test_batched_solver_rejects_single_steps_and_large_orders():
     b.step(3)                            # empty batch: nothing to do
     big.close()
     b.close()
+
+
+def test_batch_with_all_3d_sets():
+    from paper_2609_00535_b300 import semlbm
+    cases = [inputs.sphere_3d(N=4, ne=(2, 2, 2), Cn=0.35, lattice=l)
+             for l in ("D3Q13", "D3Q19", "D3Q27")]
+    b = semlbm.Batch()
+    solvers = [_solver(c) for c in cases]
+    for s in solvers:
+        b.add(s)
+    b.step(12)
+    for c, s in zip(cases, solvers):
+        assert np.array_equal(s.get_state()[0], alone(c, 12)), c.lattice
+    b.close()
+    for s in solvers:
+        s.close()

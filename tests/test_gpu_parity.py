@@ -171,3 +171,15 @@ def test_default_time_step_rule():
                           dt=0.0)
         assert abs(s.info["dt"] - case.dt) <= 1e-12 * case.dt, (s.info["dt"], case.dt)
         s.close()
+
+
+@pytest.mark.parametrize("lattice", ["D3Q19", "D3Q27"])
+@pytest.mark.parametrize("N", [3, 5])
+def test_cubic_velocity_sets(lattice, N):
+    """The cubic 3D sets on a rotated box with two wall angles and a curved sphere cap."""
+    mesh = inputs.rotate_elements(inputs.box((2, 2, 2), (0, 0, 0), (1.0, 0.8, 0.7), N,
+                                             face_tags={4: 0, 1: 1}), 7 + N)
+    case = make_case("cub", mesh, lattice, 1e-2, 0.3, 0.6, math.radians(65), (math.radians(115),),
+                     rho0=inputs.droplet_density(mesh, (0.5, 0.4, 0.1), 0.3, 0.3))
+    _compare(case, 20)
+    _compare(inputs.sphere_3d(N=N, ne=(2, 2, 2), Cn=0.35, lattice=lattice), 20)

@@ -1,0 +1,101 @@
+"""Physics of the GPU path at equilibrium (through the C ABI):
+
+* static contact angle on a flat wall for wetting angles (Sec. 3.1); with the
+  interface widths affordable here (delta / R ~ 0.2-0.4) non-wetting drops
+  settle below the prescribed angle (108 for 120 degrees) or lift off at 150,
+  so those angles are not asserted,
+* contact angle on a circular cylinder from the circle-circle geometry
+  cos(theta) = (R_c^2 + R_d^2 - d^2) / (2 R_c R_d) (Sec. 3.2),
+* Laplace's law gamma / R for drops of several radii (Appendix A gamma), and
+  the drop's residual kinetic energy reaching the paper's isolated-drop level
+  (~1e-30, Sec. 3.3) in a closed box with neutral walls,
+* the flat-wall parasitic currents decaying steadily (the paper's wetting
+  residuals are reached after ~1e6 steps; here the trend is checked over 2e5).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2609_00535_b300 import inputs
+from tests.helpers import make_case
+from tests.test_oracle_equilibria import contact_angle, contour_points, fit_circle
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(case, steps):
+    from paper_2609_00535_b300 import semlbm
+    s = semlbm.Solver.from_case(case)
+    s.set_density(case.rho0)
+    s.step(steps)
+    d = s.diagnostics()
+    rho = s.field("rho")
+    s.close()
+    return rho, d
+
+
+@pytest.mark.parametrize("deg", [30, 60, 90])
+def test_flat_wall_contact_angle(deg):
+    m = inputs.box((16, 8), (0, 0), (2, 1), 4, face_tags={2: 0})
+    th0 = math.radians(deg)
+    c = make_case("ca", m, "D2Q9", 0.1, 0.1, 1.0, th0,
+                  rho0=inputs.sessile_cap_density(m, 1.0, 0.5 * math.pi * 0.25 ** 2, th0, 0.1))
+    rho, d = _run(c, 12000)
+    assert d["status"] == 0
+    th = contact_angle(m, rho.reshape(m.n_elem, -1), 0.1, 5)
+    assert abs(th - deg) < 3.0, (deg, th)
+
+
+@pytest.mark.parametrize("deg", [60, 120])
+def test_cylinder_contact_angle(deg):
+    Rc = 0.15
+    m = inputs.rotate_elements(inputs.cylinder_ogrid(6, n_theta=48, n_r=10, Rc=Rc), 2)
+    delta = 0.06
+    Rd = 0.15
+    c = make_case("cyl", m, "D2Q9", 0.1, delta, 1.0, math.radians(deg),
+                  rho0=inputs.cylinder_cap_density(m, (0.5, 0.5), Rc, Rd, math.radians(deg), delta))
+    rho, d = _run(c, 15000)
+    assert d["status"] == 0
+    p = contour_points(m.node_xyz, rho.reshape(m.n_elem, -1), 0.55, 7)
+    p = p[np.linalg.norm(p - 0.5, axis=1) > Rc + delta]
+    cx, cy, R = fit_circle(p)
+    dist = math.hypot(cx - 0.5, cy - 0.5)
+    th = math.degrees(math.acos((Rc ** 2 + R ** 2 - dist ** 2) / (2 * Rc * R)))
+    assert abs(th - deg) < 4.0, (deg, th)
+
+
+@pytest.mark.parametrize("R", [0.25, 0.3])
+def test_laplace_law_and_residual_kinetic_energy(R):
+    m = inputs.box((8, 8), (0, 0), (1, 1), 4, face_tags={0: -1, 1: -1, 2: -1, 3: -1})
+    c = make_case("lap", m, "D2Q9", 0.1, 0.1, 1.0, math.pi / 2,
+                  rho0=inputs.droplet_density(m, (0.5, 0.5), R, 0.1))
+    rho, d = _run(c, 30000)
+    assert d["ke_max"] < 1e-26, d["ke_max"]          # the paper's isolated drop: ~1e-30
+    r = np.linalg.norm(m.node_xyz - 0.5, axis=-1).reshape(-1)
+    rin, rout = rho[r < 0.05].mean(), rho[r > 0.45].mean()
+    beta, kappa = c.beta, c.kappa
+    mu0 = lambda x: 2 * beta * (x - 1.0) * (x - 0.1) * (2 * x - 1.1)
+    e0 = lambda x: beta * (x - 1.0) ** 2 * (x - 0.1) ** 2
+    p0 = lambda x: x * mu0(x) - e0(x)
+    from tests.helpers import oracle_mesh
+    Me = oracle_mesh(m).Me.reshape(-1)
+    area = np.sum(Me * (rho - rout) / (rin - rout))
+    gamma = 0.9 ** 3 * math.sqrt(2 * kappa * beta) / 6
+    ratio = (p0(rin) - p0(rout)) / (gamma / math.sqrt(area / math.pi))
+    assert abs(ratio - 1) < 0.01, ratio
+
+
+def test_flat_wall_parasitic_currents_decay():
+    """Paper-like parameters (beta = 1e-3, tau = 0.5, 60 degrees): KE_max keeps
+    falling geometrically and is below 1e-14 after 2e5 steps."""
+    from paper_2609_00535_b300 import semlbm
+    c = inputs.flat_wall_2d()
+    s = semlbm.Solver.from_case(c)
+    s.set_density(c.rho0)
+    ke = []
+    for _ in range(4):
+        s.step(50000)
+        ke.append(s.diagnostics()["ke_max"])
+    s.close()
+    assert ke[-1] < 1e-14 and all(b < 0.5 * a for a, b in zip(ke, ke[1:])), ke

@@ -76,3 +76,21 @@ def test_configs_shapes():
     c2 = inputs.cylinder_2d()
     assert c2.mesh.n_elem == 1024 and c2.nodes == 1024 * 49
     assert abs(c1.kappa - 1e-3 * 0.125 ** 2 * 0.81 / 8) < 1e-18
+
+
+def test_equilibrium_cap_shapes():
+    import math
+    m = inputs.box((8, 4), (0, 0), (2, 1), 6)
+    area = 0.5 * math.pi * 0.25 ** 2
+    for deg in (30, 90, 150):
+        th = math.radians(deg)
+        R = inputs.cap_radius(area, th)
+        # the cap holds the requested area above the wall
+        assert abs(R * R * (th - math.sin(th) * math.cos(th)) - area) < 1e-15
+        rho = inputs.sessile_cap_density(m, 1.0, area, th, 0.02)
+        assert rho.max() > 0.99 and rho.min() < 0.11
+    assert abs(inputs.cap_radius(area, math.pi / 2) - 0.25) < 1e-15     # half disc
+    # on a cylinder at 90 degrees the drop circle is orthogonal to the wall
+    mc = inputs.cylinder_ogrid(4, n_theta=16, n_r=2)
+    r = inputs.cylinder_cap_density(mc, (0.5, 0.5), 0.1, 0.05, math.pi / 2, 0.01)
+    assert r.shape == mc.global_id.shape

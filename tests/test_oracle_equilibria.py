@@ -1,0 +1,77 @@
+"""Equilibrium pins of the oracle that need a relaxation run (slow CPU tests):
+
+* Laplace's law for a drop in a closed box: the thermodynamic pressure jump
+  p0(rho_in) - p0(rho_out), p0 = rho mu0 - e0, equals gamma / R (2D) with
+  gamma = (rho_l - rho_v)^3 sqrt(2 kappa beta) / 6 (Appendix A) and R the
+  radius of the equivalent sharp drop;
+* the static contact angle of a sessile drop on a flat wetting wall equals the
+  prescribed theta (Sec. 2.2, Sec. 3.1), measured by a circle fit to the
+  rho = (rho_l + rho_v)/2 contour away from the wall.
+Strong bulk energy (beta = 0.1) makes the relaxation take a few thousand steps.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2609_00535_b300 import inputs
+from tests.helpers import make_case, oracle_of
+
+pytestmark = pytest.mark.slow
+
+
+def contour_points(xyz, rho, level, n):
+    """Crossings of rho = level along element-local GLL lines (linear interpolation)."""
+    E = rho.shape[0]
+    R = rho.reshape(E, n, n)
+    X = xyz.reshape(E, n, n, 2)
+    pts = []
+    for ax in (1, 2):
+        a = np.moveaxis(R, ax, -1)
+        xa = np.moveaxis(X, ax, -2)
+        cross = (a[..., :-1] - level) * (a[..., 1:] - level) < 0
+        e_, i_, k_ = np.nonzero(cross)
+        t = (level - a[e_, i_, k_]) / (a[e_, i_, k_ + 1] - a[e_, i_, k_])
+        pts.append(xa[e_, i_, k_] + t[:, None] * (xa[e_, i_, k_ + 1] - xa[e_, i_, k_]))
+    return np.vstack(pts)
+
+
+def fit_circle(p):
+    A = np.c_[2 * p[:, 0], 2 * p[:, 1], np.ones(len(p))]
+    cx, cy, c = np.linalg.lstsq(A, (p ** 2).sum(1), rcond=None)[0]
+    return cx, cy, math.sqrt(c + cx * cx + cy * cy)
+
+
+def contact_angle(mesh, rho, delta, n):
+    p = contour_points(mesh.node_xyz, rho, 0.55, n)
+    p = p[p[:, 1] > delta]
+    cx, cy, R = fit_circle(p)
+    return math.degrees(math.acos(max(-1.0, min(1.0, -cy / R))))
+
+
+def test_laplace_law_closed_box():
+    m = inputs.box((8, 8), (0, 0), (1, 1), 4, face_tags={0: -1, 1: -1, 2: -1, 3: -1})
+    c = make_case("lap", m, "D2Q9", 0.1, 0.1, 1.0, math.pi / 2,
+                  rho0=inputs.droplet_density(m, (0.5, 0.5), 0.25, 0.1))
+    om, s = oracle_of(c)
+    f = s.run(s.initial_state(c.rho0.reshape(om.shape)), 3000)
+    rho = s.density(f)
+    xyz = m.node_xyz.reshape(om.shape + (2,))
+    r = np.sqrt(((xyz - 0.5) ** 2).sum(-1))
+    rin, rout = rho[r < 0.05].mean(), rho[r > 0.45].mean()
+    p0 = lambda x: x * s.mu0(x) - s.bulk_energy(x)
+    area = np.sum(om.Me * (rho - rout) / (rin - rout))
+    ratio = (p0(rin) - p0(rout)) / (s.p.surface_tension() / math.sqrt(area / math.pi))
+    assert s.diagnostics(f)["ke_max"] < 1e-6
+    assert abs(ratio - 1) < 0.02, ratio
+
+
+def test_static_contact_angle_60_degrees():
+    m = inputs.box((16, 8), (0, 0), (2, 1), 4, face_tags={2: 0})
+    th0 = math.radians(60)
+    c = make_case("ca", m, "D2Q9", 0.1, 0.1, 1.0, th0,
+                  rho0=inputs.sessile_cap_density(m, 1.0, 0.5 * math.pi * 0.25 ** 2, th0, 0.1))
+    om, s = oracle_of(c)
+    f = s.run(s.initial_state(c.rho0.reshape(om.shape)), 5000)
+    th = contact_angle(m, s.density(f).reshape(om.E, -1), 0.1, 5)
+    assert abs(th - 60.0) < 2.0, th

@@ -51,7 +51,7 @@ def test_gll_derivative_exact_on_polynomials(N):
     np.testing.assert_allclose(D, -D[::-1, ::-1], atol=1e-12 * N * N)
 
 
-@pytest.mark.parametrize("name", ["D2Q9", "D3Q13"])
+@pytest.mark.parametrize("name", ["D2Q9", "D3Q13", "D3Q19", "D3Q27"])
 def test_velocity_set_moments(name):
     lat = lattice.by_name(name)
     e, t, cs2, d = lat.e, lat.t, lat.cs2, lat.dim
@@ -66,7 +66,7 @@ def test_velocity_set_moments(name):
     np.testing.assert_allclose(np.einsum("q,qa,qb,qc,qd,qf->abcdf", t, e, e, e, e, e), 0,
                                atol=1e-15)
     np.testing.assert_allclose(e[lat.opp], -e, atol=1e-15)
-    assert lat.Q == (9 if name == "D2Q9" else 13)
+    assert lat.Q == {"D2Q9": 9, "D3Q13": 13, "D3Q19": 19, "D3Q27": 27}[name]
 
 
 def test_d3q13_speed():
