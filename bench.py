@@ -35,11 +35,11 @@ import hashlib  # noqa: E402
 METRIC = "FP64 GLL node-updates/s (3D droplet)"
 
 # DRAM traffic of one k_rhs launch from the ncu capture summarised in
-# profiles/k_rhs_sphere3d_ne12_full.md (373,248 nodes: 76.12 MB read + 8.77 MB
+# profiles/k_rhs_sphere3d_ne12_full.md (373,248 nodes: 85.08 MB read + 11.33 MB
 # written); the traffic grows with the node count, so it is scaled per node.
 # Valid only while the kernel sources are the ones that were profiled.
-RHS_TRAFFIC = {"kernels.cuh": "808e13f9e8afa8d9", "lattice.cuh": "d304ffdc1e4bb53b",
-               "bytes_per_node": (76.120064e6 + 8.773376e6) / 373248, "lattice": "D3Q13", "N": 5}
+RHS_TRAFFIC = {"kernels.cuh": "031a86c92b547a22", "lattice.cuh": "2210c9bd29fce6f9",
+               "bytes_per_node": (85.077e6 + 11.330e6) / 373248, "lattice": "D3Q13", "N": 5}
 
 
 def rhs_traffic_per_launch(lattice, N, n_local):
@@ -318,6 +318,9 @@ def native_arm(args):
     peak, _ = semlbm.fp64_peak_tflops(device)
     achieved = work["flops"] / (rhs_ms * 1e-3) / 1e12
     total_kernel_ms = sum(prof["ms"].values())
+    sw = flopcount.step_work(case.lattice, case.mesh.N, info["n_local"], info["n_global"],
+                             info["n_wall_nodes"])
+    step_s = (ms / args.steps) * 1e-3
     shares = {k: round(v / total_kernel_ms, 4) for k, v in prof["ms"].items()}
 
     # end to end through the public API with host buffers: every step uploads
@@ -377,6 +380,12 @@ def native_arm(args):
                          "peak_source": "measured live: FP64 DFMA probe (libsemlbm_peak)",
                          "fp64_op_frac": work["ops"] / (rhs_ms * 1e-3) / (peak * 1e12 / 2),
                          "kernel_ms": rhs_ms, "flops_per_launch": work["flops"]},
+            "step_roofline": {"bound": "alu", "ops_per_step": sw["ops"],
+                              "flops_per_step": sw["flops"],
+                              "achieved": sw["flops"] / step_s / 1e12, "peak": peak,
+                              "unit": "TFLOP/s", "frac": sw["flops"] / step_s / 1e12 / peak,
+                              "fp64_op_frac": sw["ops"] / step_s / (peak * 1e12 / 2),
+                              "note": "all 14 kernels of a step; counts from flops.step_work"},
             "kernel_share": shares,
             "kernel_ms_per_launch": {k: round(prof["ms"][k] / max(1, prof["launches"][k]), 4)
                                      for k in prof["ms"]},

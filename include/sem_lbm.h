@@ -96,6 +96,10 @@ typedef struct {
   void* stream;           /* cudaStream_t to run on; NULL -> solver-owned stream    */
   void* workspace;        /* caller device memory (e.g. from PyTorch) or NULL       */
   size_t workspace_bytes; /* its size; must be >= sem_lbm_workspace_bytes()         */
+  const double* wall_velocity; /* [n_tags + 1][dim]: velocity u_b of the walls with
+                             tag 0..n_tags, entering the flux bounce-back term
+                             -2 t_a rho e_a.u_b / c_s^2 (Sec. 2.2); NULL = static.
+                             Walls with tag < 0 are static.                          */
 } sem_lbm_params;
 
 typedef struct sem_lbm sem_lbm_t;

@@ -31,7 +31,8 @@ stated; they are the same readings the CUDA library implements):
  * Stage 1 uses rho and mu of fbar^n: collision conserves mass exactly, so they
    equal those of the post-collision state.
  * SSP-RK3 is the three-stage Shu-Osher form.
- * Static walls: u_b = 0 unless given.
+ * Wall velocity u_b per wall tag (static, u_b = 0, unless given); tags < 0
+   are static neutral walls.
 
 Pinned by tests/test_oracle_method.py and tests/test_oracle_brute.py (dense
 brute-force assembly on 1-4 element meshes, stationarity, mass conservation,
@@ -45,7 +46,7 @@ from .geometry import Mesh, deriv
 
 class Params:
     def __init__(self, rho_l=1.0, rho_v=0.1, beta=1e-3, kappa=None, delta=None, tau=0.5,
-                 dt=None, theta_w=np.pi / 2, theta_tag=(), mu0_factor=2.0, u_b=None):
+                 dt=None, theta_w=np.pi / 2, theta_tag=(), mu0_factor=2.0, wall_velocity=None):
         self.rho_l, self.rho_v, self.beta, self.tau = rho_l, rho_v, beta, tau
         if kappa is None:
             # Appendix A: kappa = beta delta^2 (rho_l - rho_v)^2 / 8
@@ -57,7 +58,13 @@ class Params:
         self.theta_w = theta_w
         self.theta_tag = tuple(theta_tag)
         self.mu0_factor = mu0_factor
-        self.u_b = u_b
+        self.wall_velocity = dict(wall_velocity or {})   # tag -> u_b
+
+    def u_b(self, tag, dim):
+        """Velocity of the walls with this tag (zero unless given; tags < 0 are static)."""
+        if tag < 0 or tag not in self.wall_velocity:
+            return np.zeros(dim)
+        return np.asarray(self.wall_velocity[tag], dtype=np.float64)
 
     def cos_theta(self, tag):
         """tag < 0: neutral wall (90 deg); 0: theta_w; k >= 1: theta_tag[k-1]."""
@@ -79,8 +86,7 @@ class SemLbm:
         self.mesh, self.lat, self.p = mesh, lattice, params
         self.cs2 = lattice.cs2
         self.wall_cos = np.array([params.cos_theta(int(t)) for t in mesh.wall_tag])
-        ub = np.zeros(mesh.dim) if params.u_b is None else np.asarray(params.u_b, float)
-        self.u_b = ub
+        self.wall_ub = np.array([params.u_b(int(t), mesh.dim) for t in mesh.wall_tag]).reshape(-1, mesh.dim)
         # G_bc = M_e sum_a Jinv[b,a] Jinv[c,a]: metric of the stiffness integral
         self.Gstiff = mesh.Me[..., None, None] * np.einsum("...ba,...ca->...bc", mesh.Jinv, mesh.Jinv)
 
@@ -180,7 +186,7 @@ class SemLbm:
             for a in range(lat.Q):
                 ae = m.wall_area @ lat.e[a]       # w_face * |a| * n.e_a
                 inc = ae < 0
-                bc = gw[a] - gw[lat.opp[a]] - 2 * lat.t[a] / cs2 * rw * (lat.e[a] @ self.u_b)
+                bc = gw[a] - gw[lat.opp[a]] - 2 * lat.t[a] / cs2 * rw * (self.wall_ub @ lat.e[a])
                 flux[a] = np.where(inc, ae * bc, 0.0)
             r = m.add_wall_nodes(r, flux)
         return np.stack([m.dss_average(r[a]) for a in range(lat.Q)])

@@ -186,7 +186,8 @@ __global__ void k_wall_setup(const double* __restrict__ xyz, const double* __res
                              const double* __restrict__ wgll, const int* __restrict__ rec_elem,
                              const int* __restrict__ rec_node, const double* __restrict__ rec_cos,
                              const int* __restrict__ rec_mask, int R, double sq2bk,
-                             double* __restrict__ wet, double* __restrict__ ae) {
+                             const double* __restrict__ rec_ub, double* __restrict__ wet,
+                             double* __restrict__ ae, double* __restrict__ wub) {
   constexpr int D = L::D, NL = ipow(NP, D);
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= R) return;
@@ -215,8 +216,8 @@ __global__ void k_wall_setup(const double* __restrict__ xyz, const double* __res
     }
   }
   double wsum = 0.0;
-  double acc[L::Q];
-  for (int q = 0; q < L::Q; ++q) acc[q] = 0.0;
+  double acc[L::Q], accu[L::Q];
+  for (int q = 0; q < L::Q; ++q) acc[q] = accu[q] = 0.0;
   for (int f = 0; f < 2 * D; ++f) {
     if (!((mask >> f) & 1)) continue;
     const int b = f >> 1;
@@ -236,11 +237,20 @@ __global__ void k_wall_setup(const double* __restrict__ xyz, const double* __res
       for (int c = 0; c < D; ++c) dot += L::C(q, c) * a[c];
       dot *= L::S;
       // tangential directions (a . e = 0 up to rounding) are not incoming
-      if (dot < -1e-13 * an * L::SPEED_MAX) acc[q] += dot;
+      if (dot < -1e-13 * an * L::SPEED_MAX) {
+        acc[q] += dot;
+        if (rec_ub) {   // this face's wall velocity: -2 t e.u_b / c_s^2 times w (a.e)
+          double eu = 0.0;
+          for (int c = 0; c < D; ++c) eu += L::C(q, c) * rec_ub[((int64_t)r * 2 * D + f) * D + c];
+          accu[q] += dot * (-2.0 * kInvCs2 * L::t(q) * L::S * eu);
+        }
+      }
     }
   }
   wet[r] = wsum;
   for (int q = 0; q < L::Q; ++q) ae[(int64_t)q * R + r] = acc[q];
+  if (wub)
+    for (int q = 0; q < L::Q; ++q) wub[(int64_t)q * R + r] = accu[q];
 }
 
 // ---------------------------------------------------------------------------
@@ -256,7 +266,8 @@ struct View {
   const double *Jinv, *Gm, *Me, *invMg, *Dm;      // geometry, GLL derivative matrix
   const int *off, *idx, *wslot;                    // gather-scatter CSR, wall slots
   const double *wet, *ae;                          // wall records
-  int R, E, G, pad;
+  const double* wub;   // [Q][R] flux bounce-back wall-velocity coefficients (or unused)
+  int R, E, G, has_ub;
   int64_t V;
   double dt, omega, kappa, fbeta, rho_l, rho_v;    // omega = 1/(tau + 1/2), fbeta = mu0 factor * beta
 };
@@ -520,7 +531,8 @@ __device__ __forceinline__ void body_rhs(const View& v, const double* __restrict
 #pragma unroll
   for (int b = 0; b < D; ++b) dr[b] = v.drho[b * V + idx];
   grad_ref<D, NP>(Dr, ix, smu + lb, k, dm);
-  const double rh3 = kInvCs2 * sr[lb + k];
+  const double rh_node = sr[lb + k];
+  const double rh3 = kInvCs2 * rh_node;
   double vv[D];   // d_b rho - (rho / c_s^2) d_b mu, reference components
 #pragma unroll
   for (int b = 0; b < D; ++b) vv[b] = fma(-rh3, dm[b], dr[b]);
@@ -552,6 +564,10 @@ __device__ __forceinline__ void body_rhs(const View& v, const double* __restrict
       const double gA = sg[(A - 1) * NT + lb + k], gB = sg[(B - 1) * NT + lb + k];
       rA = fma(__ldg(wae + (int64_t)A * R + slot), gA - gB, rA);
       rB = fma(__ldg(wae + (int64_t)B * R + slot), gB - gA, rB);
+      if (v.has_ub) {   // moving walls: -2 t rho e.u_b / c_s^2 on incoming directions
+        rA = fma(__ldg(v.wub + (int64_t)A * R + slot), rh_node, rA);
+        rB = fma(__ldg(v.wub + (int64_t)B * R + slot), rh_node, rB);
+      }
     }
     r[A * V + idx] = rA;
     r[B * V + idx] = rB;

@@ -90,6 +90,8 @@ struct HostMaps {
   std::vector<int> slot;              // [V] wall record or -1
   std::vector<int> rec_elem, rec_node, rec_mask;
   std::vector<double> rec_cos;        // [R][2D]
+  std::vector<double> rec_ub;         // [R][2D][D] wall velocity of each face (moving walls)
+  bool moving = false;
   int64_t G = 0;
 };
 
@@ -132,7 +134,11 @@ int build_maps(const sem_lbm_mesh* m, int N, double theta_w, const sem_lbm_param
   };
   h.slot.assign(V, -1);
   std::vector<int> mask(NL);
-  std::vector<double> cosf(2 * D);
+  std::vector<double> cosf(2 * D), ubf(2 * D * D);
+  auto ub_of = [&](int tag, double* u) {   // velocity of the walls with this tag
+    for (int c = 0; c < D; ++c)
+      u[c] = (tag >= 0 && p && p->wall_velocity && tag <= p->n_tags) ? p->wall_velocity[tag * D + c] : 0.0;
+  };
   for (int64_t e = 0; e < E; ++e) {
     bool any = false;
     for (int f = 0; f < 2 * D; ++f) {
@@ -141,8 +147,11 @@ int build_maps(const sem_lbm_mesh* m, int N, double theta_w, const sem_lbm_param
       if (k == 1) {
         any = true;
         if (int rc = cos_of(m->face_tag[e * 2 * D + f], &cosf[f])) return rc;
+        ub_of(m->face_tag[e * 2 * D + f], &ubf[f * D]);
+        for (int c = 0; c < D; ++c) h.moving = h.moving || ubf[f * D + c] != 0.0;
       } else {
         cosf[f] = 0.0;
+        for (int c = 0; c < D; ++c) ubf[f * D + c] = 0.0;
       }
     }
     if (!any) continue;
@@ -162,6 +171,7 @@ int build_maps(const sem_lbm_mesh* m, int N, double theta_w, const sem_lbm_param
       h.rec_node.push_back(k);
       h.rec_mask.push_back(mask[k]);
       for (int f = 0; f < 2 * D; ++f) h.rec_cos.push_back(cosf[f]);
+      h.rec_ub.insert(h.rec_ub.end(), ubf.begin(), ubf.end());
     }
   }
   return 0;
@@ -276,7 +286,8 @@ struct Impl {
     if (s.R == 0) return;
     k_wall_setup<L, NP><<<grid_of(s.R, 128), 128, 0, s.stream>>>(
         s.xyz, s.Dm, s.wg, s.rec_elem, s.rec_node, s.rec_cos, s.rec_mask, (int)s.R,
-        std::sqrt(2.0 * s.beta / s.kappa), s.wet, s.ae);
+        std::sqrt(2.0 * s.beta / s.kappa), s.moving ? s.rec_ub : nullptr, s.wet, s.ae,
+        s.moving ? s.wub : nullptr);
   }
   static void lap(sem_lbm& s) {
     k_lap<L, NP, EPB><<<blocks(s), THREADS, SM_LAP, s.stream>>>(s.view, s.rho, s.lapr, s.drho);
@@ -417,6 +428,8 @@ size_t layout(sem_lbm& s, char* base) {
   s.rec_node = c.take<int>(R);
   s.rec_mask = c.take<int>(R);
   s.rec_cos = c.take<double>(R * 2 * D);
+  s.rec_ub = c.take<double>(R * 2 * D * D);   // wall records only: small
+  s.wub = c.take<double>(Q * R);
   s.flags = c.take<int>(8);
   s.parts = c.take<DiagPart>(s.diag_blocks);
   s.dout = c.take<DiagPart>(1);
@@ -430,7 +443,9 @@ void fill_view(sem_lbm& s) {
   v.flags = s.flags;
   v.Jinv = s.Jinv; v.Gm = s.Gm; v.Me = s.Me; v.invMg = s.invMg; v.Dm = s.Dm;
   v.off = s.off; v.idx = s.idx; v.wslot = s.slot; v.wet = s.wet; v.ae = s.ae;
-  v.R = (int)s.R; v.E = (int)s.E; v.G = (int)s.G; v.pad = 0;
+  v.R = (int)s.R; v.E = (int)s.E; v.G = (int)s.G;
+  v.wub = s.wub;
+  v.has_ub = s.moving ? 1 : 0;
   v.V = s.V;
   v.dt = s.dt;
   v.omega = 1.0 / (s.tau + 0.5);
@@ -506,6 +521,7 @@ int sem_lbm_create(const sem_lbm_mesh* mesh, int N, sem_lbm_lattice lattice, dou
   s->V = s->E * s->NL;
   s->G = h.G;
   s->R = (int64_t)h.rec_elem.size();
+  s->moving = h.moving;
   s->beta = beta;
   s->kappa = kappa;
   s->tau = tau;
@@ -572,7 +588,8 @@ int sem_lbm_create(const sem_lbm_mesh* mesh, int N, sem_lbm_lattice lattice, dou
             up(s->slot, h.slot.data(), sizeof(int) * s->V) &&
             cudaMemsetAsync(s->flags, 0, 8 * sizeof(int), st) == cudaSuccess;
   if (ok && s->R > 0)
-    ok = up(s->rec_elem, h.rec_elem.data(), sizeof(int) * s->R) &&
+    ok = (!s->moving || up(s->rec_ub, h.rec_ub.data(), sizeof(double) * s->R * 2 * D * D)) &&
+         up(s->rec_elem, h.rec_elem.data(), sizeof(int) * s->R) &&
          up(s->rec_node, h.rec_node.data(), sizeof(int) * s->R) &&
          up(s->rec_mask, h.rec_mask.data(), sizeof(int) * s->R) &&
          up(s->rec_cos, h.rec_cos.data(), sizeof(double) * s->R * 2 * D);

@@ -44,7 +44,8 @@ struct sem_lbm {
   // device arrays
   double *f, *fs, *g, *r, *rho, *mu, *lapr, *Fp, *drho, *Jinv, *Gm, *Me, *invMg, *xyz, *Dm, *wg;
   int *off, *idx, *slot, *rec_elem, *rec_node, *rec_mask, *flags;
-  double *wet, *ae, *rec_cos;
+  double *wet, *ae, *rec_cos, *rec_ub, *wub;
+  bool moving = false;   // some wall has a non-zero velocity
   semlbm::DiagPart *parts, *dout;
   int diag_blocks = 0;
   bool state_ready = false;

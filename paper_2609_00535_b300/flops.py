@@ -74,3 +74,60 @@ def rhs_bytes_per_node(lattice, N):
     d = _DIM[lattice]
     Q = 2 * len(_REP_NONZERO[lattice]) + 1
     return 8 * ((Q - 1) + 2 + d + d * d + 1 + (Q - 1)) + 4
+
+
+# ---------------------------------------------------------------------------
+# FP64 work of one whole time step (all 14 kernels), for the step roofline.
+# Per element-local node (V of them), per node group (G; a group is one mesh
+# node, summed over its copies), per extra copy (V - G) and per wall record R.
+# A double division counts as one operation.
+# ---------------------------------------------------------------------------
+def _cdot_ops(lattice):
+    """FP64 ops of C_a . v for each representative velocity."""
+    if lattice == "D3Q13":
+        return [1] * 6                       # one fma with phi
+    return [k - 1 for k in _REP_NONZERO[lattice]]
+
+
+def step_work(lattice, N, n_local, n_groups, n_wall_nodes):
+    """(ops, flops) of the 14 kernels of one time step."""
+    n, d = N + 1, _DIM[lattice]
+    Q = 2 * len(_REP_NONZERO[lattice]) + 1
+    M = Q - 1
+    V, G, R = n_local, n_groups, n_wall_nodes
+    X = V - G                                  # extra copies of shared nodes
+    S1 = 0 if lattice in ("D2Q9", "D3Q19", "D3Q27") else 1   # |e| scale multiplies
+    dv = _deriv(n)
+    ops = flops = 0
+
+    def add(o, f, count):
+        nonlocal ops, flops
+        ops += o * count
+        flops += f * count
+
+    # k_lap (x3): grad rho, metric products, D^T contraction; wall wetting term
+    add(2 * d * dv["ops"] + d * d + (d - 1),
+        2 * d * dv["flops"] + d * (2 * d - 1) + (d - 1), 3 * V)
+    add(4, 5, 3 * R)
+    # k_dss_mu (x3): sum of copies, 1/M, mu0 and -kappa lap
+    add(10, 11, 3 * G)
+    add(1, 1, 3 * X)
+    # k_force (x1): grad mu, physical gradients, M_e (c^2 grad rho - rho grad mu)
+    add(d * dv["ops"] + 2 * d * d + 3 * d,
+        d * dv["flops"] + 2 * d * (2 * d - 1) + 4 * d, V)
+    # k_dss_collide (x1): force average, momentum, equilibrium and F**
+    cd = _cdot_ops(lattice)
+    mom = sum(1 + k for k in _REP_NONZERO[lattice])            # difference + components
+    per_group = d + mom + 1 + d + 2 * (2 * d - 1) + 1 + 4 + 4
+    per_group += sum(2 * c + S1 + 1 + 1 + 2 + 1 + 8 for c in cd)
+    add(per_group, per_group + 8 * len(cd) + 6, G)
+    add(d, d, X)
+    # k_rhs (x3)
+    w = rhs_work_per_node(lattice, N)
+    add(w["ops"], w["flops"], 3 * V)
+    add(2 * M, 3 * M, 3 * R)
+    # k_dss_rk (x3): sums of copies, dt/M, stage update, rho
+    add(M, M, 3 * X)
+    add(1 + M + Q, 1 + 2 * M + Q, G)                          # stage 1
+    add(2 * (2 + 3 * M + 2 + Q), 2 * (2 + 5 * M + 3 + Q), G)  # stages 2 and 3
+    return {"ops": ops, "flops": flops}

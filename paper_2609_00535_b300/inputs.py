@@ -294,6 +294,7 @@ class Case:
     rho0: np.ndarray = None
     steps: int = 0
     extra: dict = field(default_factory=dict)
+    wall_velocity: dict = field(default_factory=dict)   # wall tag -> u_b
 
     @property
     def nodes(self):

@@ -50,7 +50,7 @@ class ParamsC(ctypes.Structure):
                 ("cfl", ctypes.c_double), ("mu0_factor", ctypes.c_double),
                 ("n_tags", ctypes.c_int), ("theta_tag", ctypes.c_void_p),
                 ("stream", ctypes.c_void_p), ("workspace", ctypes.c_void_p),
-                ("workspace_bytes", ctypes.c_size_t)]
+                ("workspace_bytes", ctypes.c_size_t), ("wall_velocity", ctypes.c_void_p)]
 
 
 class DiagC(ctypes.Structure):
@@ -182,7 +182,8 @@ class Solver:
     """One SEM-LBM solve on one GPU: create / set_density / step / diagnostics."""
 
     def __init__(self, mesh, lattice, beta, kappa, tau, theta_w, theta_tag=(), rho_l=1.0,
-                 rho_v=0.1, dt=0.0, cfl=0.0, mu0_factor=0.0, stream=None, device=0):
+                 rho_v=0.1, dt=0.0, cfl=0.0, mu0_factor=0.0, stream=None, device=0,
+                 wall_velocity=None):
         import torch
         L = load()
         self.lattice = LATTICES.get(lattice, lattice)
@@ -198,9 +199,16 @@ class Solver:
             raise SemLbmError(-1, L.sem_lbm_last_error().decode())
         self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
         self._tags = np.ascontiguousarray(np.asarray(theta_tag, dtype=np.float64).reshape(-1))
+        self._ub = None
+        if wall_velocity:   # {tag: u_b} for tags 0..len(theta_tag)
+            self._ub = np.zeros((len(self._tags) + 1, self.dim))
+            for tag, u in dict(wall_velocity).items():
+                if 0 <= int(tag) <= len(self._tags):
+                    self._ub[int(tag)] = u
         p = ParamsC(rho_l, rho_v, dt, cfl, mu0_factor, len(self._tags),
                     self._tags.ctypes.data if len(self._tags) else None,
-                    self.stream.cuda_stream, self.workspace.data_ptr(), nbytes)
+                    self.stream.cuda_stream, self.workspace.data_ptr(), nbytes,
+                    self._ub.ctypes.data if self._ub is not None else None)
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             check(L.sem_lbm_create(ctypes.byref(m), self.N, self.lattice, beta, kappa, tau,
@@ -212,7 +220,8 @@ class Solver:
     @classmethod
     def from_case(cls, case, **kw):
         return cls(case.mesh, case.lattice, case.beta, case.kappa, case.tau, case.theta_w,
-                   case.theta_tag, case.rho_l, case.rho_v, dt=case.dt, **kw)
+                   case.theta_tag, case.rho_l, case.rho_v, dt=case.dt,
+                   wall_velocity=getattr(case, "wall_velocity", None), **kw)
 
     # -- state -------------------------------------------------------------
     def set_density(self, rho):

@@ -143,3 +143,22 @@ def test_batch_with_all_3d_sets():
     b.close()
     for s in solvers:
         s.close()
+
+
+def test_batch_with_moving_wall_member():
+    from paper_2609_00535_b300 import semlbm
+    m = inputs.box((4, 3), (0, 0), (1, 0.8), 4, face_tags={2: 0, 3: 1})
+    moving = make_case("lid", m, "D2Q9", 1e-2, 0.25, 0.7, math.radians(60), (math.pi / 2,),
+                       rho0=inputs.droplet_density(m, (0.5, 0.0), 0.35, 0.25),
+                       wall_velocity={1: (0.02, 0.0)})
+    cases = [moving, mix()[0]]            # same (D2Q9, N=4) group, one static
+    b = semlbm.Batch()
+    solvers = [_solver(c) for c in cases]
+    for s in solvers:
+        b.add(s)
+    b.step(15)
+    for c, s in zip(cases, solvers):
+        assert np.array_equal(s.get_state()[0], alone(c, 15))
+    b.close()
+    for s in solvers:
+        s.close()

@@ -183,3 +183,34 @@ def test_cubic_velocity_sets(lattice, N):
                      rho0=inputs.droplet_density(mesh, (0.5, 0.4, 0.1), 0.3, 0.3))
     _compare(case, 20)
     _compare(inputs.sphere_3d(N=N, ne=(2, 2, 2), Cn=0.35, lattice=lattice), 20)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_moving_wall_lid_driven(dim):
+    """Flux bounce-back with a sliding lid (tag 1) next to a wetting wall (tag 0)."""
+    if dim == 2:
+        mesh = inputs.rotate_elements(inputs.box((4, 3), (0, 0), (1, 0.8), 5, face_tags={2: 0, 3: 1}), 3)
+        lat, x0, ub = "D2Q9", (0.5, 0.0), (0.02, 0.0)
+    else:
+        mesh = inputs.rotate_elements(inputs.box((2, 2, 2), (0, 0, 0), (1, 1, 0.8), 4,
+                                                 face_tags={4: 0, 5: 1}), 4)
+        lat, x0, ub = "D3Q13", (0.5, 0.5, 0.0), (0.02, -0.01, 0.0)
+    case = make_case("lid", mesh, lat, 1e-2, 0.25, 0.7, math.radians(60), (math.pi / 2,),
+                     rho0=inputs.droplet_density(mesh, x0, 0.35, 0.25), wall_velocity={1: ub})
+    _compare(case, 150 if dim == 2 else 40)
+
+
+def test_couette_profile_on_gpu():
+    from paper_2609_00535_b300 import semlbm
+    H, U = 0.5, 1e-3
+    m = inputs.box((2, 8), (0, 0), (0.25, H), 4, periodic=(True, False), face_tags={3: 0})
+    c = make_case("couette", m, "D2Q9", 1e-3, 0.05, 2.0, math.pi / 2,
+                  rho0=np.full(m.global_id.shape, 1.0), wall_velocity={0: (U, 0.0)})
+    s = semlbm.Solver.from_case(c)
+    s.set_density(c.rho0)
+    nu = c.tau * c.dt / 3.0
+    s.step(int(12 * H * H / (math.pi ** 2 * nu) / c.dt))
+    u = s.field("u")
+    y = m.node_xyz[..., 1].reshape(-1)
+    assert np.abs(u[0] - U * y / H).max() < 1e-4 * U
+    s.close()

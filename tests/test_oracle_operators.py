@@ -44,7 +44,8 @@ def smooth_field(xyz, k, periodic_L=None):
 def build(name, mesh, beta=2e-3, delta=0.2, thetas=(math.radians(60), math.radians(125))):
     lat = lattice.d2q9() if mesh.dim == 2 else lattice.d3q13()
     p = method.Params(beta=beta, delta=delta, dt=0.01, tau=0.7, theta_w=thetas[0],
-                      theta_tag=thetas[1:])
+                      theta_tag=thetas[1:],
+                      wall_velocity={1: [0.03, -0.02, 0.01][:mesh.dim]})   # tag 1 slides
     om = oracle_mesh(mesh)
     return om, method.SemLbm(om, lat, p), Dense(mesh)
 
@@ -122,7 +123,9 @@ def test_streaming_rhs_dense(name):
         def bb(el, sel, nrm, tag):
             ne = nrm @ e
             idx = dn.gmap[el][sel]
-            return np.where(ne < -1e-12, ne * (ga[idx] - gb[idx]), 0.0)
+            ub = s.p.u_b(tag, mesh.dim)
+            jump = ga[idx] - gb[idx] - 2 * t / cs2 * rg[idx] * (e @ ub)
+            return np.where(ne < -1e-12, ne * jump, 0.0)
 
         rhs = -dn.convection(e) @ (ga - t * rg) - (t / cs2) * dn.convection(e, weight=rg) @ mg
         rhs = rhs + dn.wall_vector(bb)

@@ -142,3 +142,23 @@ def test_collision_conserves_mass_and_momentum():
     np.testing.assert_allclose(fs.sum(0), rho, rtol=1e-15)
     np.testing.assert_allclose(np.einsum("q...,qa->...a", fs, s.lat.e),
                                np.einsum("q...,qa->...a", f, s.lat.e), atol=1e-16)
+
+
+def test_couette_flow_between_a_static_and_a_sliding_wall():
+    """Single phase between y = 0 (static) and y = H (tag 0, sliding at U):
+    the steady flux bounce-back solution is the linear profile u_x = U y / H
+    (no slip on both walls, Sec. 2.2)."""
+    H, U = 0.25, 1e-3
+    m = inputs.box((2, 4), (0, 0), (0.25, H), 4, periodic=(True, False), face_tags={3: 0})
+    c = make_case("couette", m, "D2Q9", 1e-3, 0.05, 2.0, math.pi / 2,
+                  rho0=np.full(m.global_id.shape, 1.0), wall_velocity={0: (U, 0.0)})
+    om, s = oracle_of(c)
+    f = s.initial_state(c.rho0.reshape(om.shape))
+    nu = c.tau * c.dt / 3.0
+    steps = int(6 * H * H / (math.pi ** 2 * nu) / c.dt)      # six slowest decay times
+    f = s.run(f, steps)
+    u = s.velocity(f, s.density(f)).reshape(-1, 2)
+    y = m.node_xyz[..., 1].reshape(-1)
+    assert np.abs(u[:, 0] - U * y / H).max() < 2e-3 * U
+    assert np.abs(u[:, 1]).max() < 1e-6 * U
+    assert abs(s.diagnostics(f)["mass"] - s.diagnostics(s.initial_state(c.rho0.reshape(om.shape)))["mass"]) < 1e-13
