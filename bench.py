@@ -51,6 +51,8 @@ def rhs_traffic_per_launch(lattice, N, n_local):
     if (lattice, N) != (RHS_TRAFFIC["lattice"], RHS_TRAFFIC["N"]):
         return None
     return RHS_TRAFFIC["bytes_per_node"] * n_local
+
+
 UNIT = "node-updates/s"
 L2_BYTES = 126 * 2 ** 20
 
@@ -261,6 +263,31 @@ def serving_section(args, device, capacity):
     return out
 
 
+def converging_serving_section(args, device):
+    """A stream of drop-radius sweep requests each run until KE_max < 1e-20."""
+    from paper_2609_00535_b300 import serve
+    reqs = inputs.converging_request_stream(n=args.converge_requests, rate=args.converge_rate,
+                                            seed=6)
+    srv = serve.Server(hbm_budget_bytes=int(args.serve_budget_gb * 2 ** 30), epoch_steps=500,
+                       ke_tol=1e-20, max_steps=60000, min_steps=1000)
+    st = srv.run(reqs)
+    out = st.summary()
+    steps = sorted(r.steps for r in st.records if r.finished is not None)
+    shapes = {}
+    for r in st.records:
+        key = r.name.rsplit("-", 1)[0]
+        e = shapes.setdefault(key, {"requests": 0, "converged": 0, "max_steps": 0})
+        e["requests"] += 1
+        e["converged"] += int(r.converged)
+        e["max_steps"] = max(e["max_steps"], r.steps)
+    out.update({"workload": "closed-box drops 2D, 6x6..9x9 elements at N 4, 6x6 at N 5, "
+                            "R 0.22-0.30, beta 0.1",
+                "by_shape": shapes,
+                "arrival_rate_per_s": args.converge_rate, "ke_tol": 1e-20, "max_steps": 60000,
+                "epoch_steps": 500, "median_steps_to_converge": steps[len(steps) // 2] if steps else None})
+    return out
+
+
 def native_arm(args):
     import numpy as np
     import torch
@@ -357,9 +384,11 @@ def native_arm(args):
         batched = serving = None
         if not args.no_batched:
             batched = batched_section(args, device)
+        serving_converge = None
         if not args.no_serving:
             cap = batched["batched_node_updates_per_s"] if batched else value
             serving = serving_section(args, device, cap)
+            serving_converge = converging_serving_section(args, device)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -396,6 +425,7 @@ def native_arm(args):
             "cpu_baseline": cpu,
             "batched": batched,
             "serving": serving,
+            "serving_to_convergence": serving_converge,
             "final_diag": {"ke_max": d["ke_max"], "mass": d["mass"], "status": d["status"]},
         }
         print(json.dumps(line), flush=True)
@@ -422,6 +452,8 @@ def main():
     ap.add_argument("--serve-max-steps", type=int, default=300)
     ap.add_argument("--serve-epoch", type=int, default=50)
     ap.add_argument("--serve-budget-gb", type=float, default=40.0)
+    ap.add_argument("--converge-requests", type=int, default=100)
+    ap.add_argument("--converge-rate", type=float, default=20.0)
     ap.add_argument("--ne", type=int, default=None,
                     help="elements per axis of the sphere-cap mesh (profiling cases only)")
     args = ap.parse_args()

@@ -407,10 +407,24 @@ def mixed_case(rng, kind, E, N, theta, radius_scale=1.0):
     elif kind == "droplet3d":
         ne = max(2, int(round(E ** (1.0 / 3.0))))
         c = periodic_droplet(dim=3, ne=ne, N=N, D=0.5 * radius_scale, Cn=max(0.063, 4.0 / (ne * N)))
+    elif kind == "boxdrop2d":
+        c = closed_box_drop(N=N, ne=max(4, int(round(math.sqrt(E)))), R=0.25 * radius_scale)
     else:
         raise ValueError(kind)
     c.name = "%s-E%d-N%d-%.0fdeg" % (kind, c.mesh.n_elem, N, math.degrees(theta))
     return c
+
+
+def closed_box_drop(N=4, ne=8, R=0.25, beta=0.1, delta=0.1, tau=1.0, rho_l=1.0, rho_v=0.1,
+                    cfl=0.4):
+    """Drop in the unit box with neutral no-slip walls: relaxes to its Laplace
+    equilibrium, with KE_max below 1e-20 after ~2e4 steps at these parameters."""
+    mesh = box((ne, ne), (0.0, 0.0), (1.0, 1.0), N, face_tags={0: -1, 1: -1, 2: -1, 3: -1})
+    kappa = kappa_from_width(beta, delta, rho_l, rho_v)
+    rho0 = droplet_density(mesh, (0.5, 0.5), R, delta, rho_l, rho_v)
+    return Case("boxdrop2d", mesh, "D2Q9", rho_l, rho_v, beta, kappa, tau,
+                cfl_dt(mesh, "D2Q9", cfl, kappa, rho_l), math.pi / 2, (), rho0, 0,
+                {"delta": delta})
 
 
 def batch_mix(n=64, seed=4, elems=(256, 4096), orders=(4, 5, 6, 7, 8)):
@@ -491,3 +505,21 @@ def cylinder_cap_density(mesh, center, Rc, Rd, theta, delta, rho_l=1.0, rho_v=0.
     c = np.asarray(center, dtype=np.float64) + np.array([0.0, d])
     dist = np.sqrt(((mesh.node_xyz - c) ** 2).sum(-1)) - Rd
     return tanh_profile(dist, delta, rho_l, rho_v)
+
+
+def converging_request_stream(n=100, rate=20.0, seed=6,
+                              shapes=((6, 4), (7, 4), (8, 4), (9, 4), (6, 5))):
+    """Poisson stream of drop-radius sweep requests that relax to KE_max < 1e-20:
+    closed-box drops, R = 0.25 x [0.88, 1.2], (elements per side, N) uniform over
+    `shapes`, which keep dt within a factor ~2 of each other (the viscosity is
+    proportional to tau dt, so the steps to converge grow like 1/dt^2: 10x10
+    quads at N = 4 or 7x7 at N = 5 need more than 6e4)."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for i in range(n):
+        t += rng.exponential(1.0 / rate)
+        ne, N = shapes[int(rng.integers(len(shapes)))]
+        out.append(Request(i, t, "boxdrop2d", ne * ne, N, math.pi / 2,
+                           float(rng.uniform(0.88, 1.2)), int(rng.integers(1 << 30))))
+    return out

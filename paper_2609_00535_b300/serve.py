@@ -44,6 +44,7 @@ class Record:
     nodes: int = 0
     bytes: int = 0
     name: str = ""
+    error: str = ""
     state: object = None
 
 
@@ -78,6 +79,8 @@ class Stats:
             "node_updates_per_s": self.node_updates / self.wall_s if self.wall_s else None,
             "wall_s": self.wall_s, "epochs": self.epochs, "max_slots": self.max_slots,
             "max_bytes": self.max_bytes, "overlapped_admissions": self.overlapped_admissions,
+            "failures": [{"name": r.name, "steps": r.steps, "error": r.error}
+                         for r in done if r.failed],
         }
 
 
@@ -153,7 +156,7 @@ class Server:
             except Exception as exc:   # a request that cannot be built fails alone
                 rec.failed = True
                 rec.finished = self.clock() - t0
-                rec.name = rec.name or repr(exc)
+                rec.error = repr(exc)[:200]
                 ready.put((req.rid, None))
 
         pool = cf.ThreadPoolExecutor(max_workers=self.workers)
@@ -206,6 +209,7 @@ class Server:
                     rec.steps, rec.ke_max = d["step"], d["ke_max"]
                     if d["status"] != 0:
                         rec.failed = True
+                        rec.error = "status %d at step %d" % (d["status"], d["step"])
                     elif d["step"] >= self.min_steps and d["ke_max"] < self.ke_tol:
                         rec.converged = True
                     elif d["step"] < self.max_steps:

@@ -39,3 +39,23 @@ def test_budget_limits_concurrent_slots():
     st = Server(hbm_budget_bytes=int(1.5 * one), epoch_steps=10, ke_tol=0.0, max_steps=30,
                 min_steps=10).run(reqs)
     assert st.summary()["completed"] == 4 and st.max_slots == 1
+
+
+def test_requests_run_to_convergence():
+    """Closed-box drops relax to KE_max < 1e-20; each retires on convergence,
+    not on the step cap, and its final state is the one it reaches alone."""
+    from paper_2609_00535_b300 import semlbm
+    reqs = inputs.converging_request_stream(n=4, rate=50.0, seed=9, shapes=((6, 4),))
+    st = Server(hbm_budget_bytes=2 << 30, epoch_steps=500, ke_tol=1e-20, max_steps=60000,
+                min_steps=1000, keep_state=True).run(reqs)
+    summ = st.summary()
+    assert summ["completed"] == 4 and summ["converged"] == 4, summ
+    for req, rec in zip(reqs, st.records):
+        assert rec.ke_max < 1e-20 and rec.steps < 60000
+        case = req.case()
+        s = semlbm.Solver.from_case(case)
+        s.set_density(case.rho0)
+        s.step(rec.steps)
+        assert np.array_equal(s.get_state()[0], rec.state), rec.name
+        assert s.diagnostics()["ke_max"] < 1e-20
+        s.close()

@@ -94,3 +94,14 @@ def test_equilibrium_cap_shapes():
     mc = inputs.cylinder_ogrid(4, n_theta=16, n_r=2)
     r = inputs.cylinder_cap_density(mc, (0.5, 0.5), 0.1, 0.05, math.pi / 2, 0.01)
     assert r.shape == mc.global_id.shape
+
+
+def test_converging_request_stream():
+    reqs = inputs.converging_request_stream(n=20, rate=10.0, seed=3)
+    assert [r.rid for r in reqs] == list(range(20))
+    assert all(b.arrival > a.arrival for a, b in zip(reqs, reqs[1:]))
+    for r in reqs[:4]:
+        c = r.case()
+        assert c.name.startswith("boxdrop2d") and c.lattice == "D2Q9" and c.theta_tag == ()
+        assert (c.mesh.face_kind == 1).sum() == 4 * int(round(math.sqrt(r.E))) and c.dt > 1e-3
+        assert abs(c.rho0.max() - c.rho_l) < 1e-3 and abs(c.rho0.min() - c.rho_v) < 1e-3
