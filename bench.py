@@ -38,8 +38,8 @@ METRIC = "FP64 GLL node-updates/s (3D droplet)"
 # profiles/k_rhs_sphere3d_ne12_full.md (373,248 nodes: 85.08 MB read + 11.33 MB
 # written); the traffic grows with the node count, so it is scaled per node.
 # Valid only while the kernel sources are the ones that were profiled.
-RHS_TRAFFIC = {"kernels.cuh": "031a86c92b547a22", "lattice.cuh": "2210c9bd29fce6f9",
-               "bytes_per_node": (85.077e6 + 11.330e6) / 373248, "lattice": "D3Q13", "N": 5}
+RHS_TRAFFIC = {"kernels.cuh": "ed260f313d916e09", "lattice.cuh": "2210c9bd29fce6f9",
+               "bytes_per_node": (82.10e6 + 11.93e6) / 373248, "lattice": "D3Q13", "N": 5}
 
 
 def rhs_traffic_per_launch(lattice, N, n_local):

@@ -100,11 +100,13 @@ __device__ __forceinline__ bool nonfinite(double x) {
 }
 
 // ---------------------------------------------------------------------------
-// setup: geometry per node (Jacobian by D on the coordinates), Eq. (spetrum) M
+// setup: geometry per node (Jacobian by D on the coordinates), Eq. (spetrum) M;
+// MJ = M_e S J^-1 (S = the velocity set's speed scale) is the metric of the
+// force and the streaming right-hand side, with the mass and the speed folded in
 // ---------------------------------------------------------------------------
 template <int D, int NP, int EPB>
 __global__ void __launch_bounds__(cta_threads<D, NP, EPB>()) k_geom(const double* __restrict__ xyz, const double* __restrict__ Dmat,
-                       const double* __restrict__ wgll, double* __restrict__ Jinv,
+                       const double* __restrict__ wgll, double scale, double* __restrict__ MJ,
                        double* __restrict__ Gm, double* __restrict__ Me, int* __restrict__ bad,
                        int64_t V, int E) {
   constexpr int NL = ipow(NP, D), NT = EPB * NL;
@@ -150,16 +152,17 @@ __global__ void __launch_bounds__(cta_threads<D, NP, EPB>()) k_geom(const double
   if (!(det > 0.0)) atomicOr(bad, 1);
   const double inv = 1.0 / det;
   const int64_t idx = base + tid;
-  double Ji[3][3];
-  for (int b = 0; b < D; ++b)
-    for (int a = 0; a < D; ++a) {
-      Ji[b][a] = adj[b][a] * inv;                        // dxi_b / dx_a
-      Jinv[(b * D + a) * V + idx] = Ji[b][a];
-    }
   double W = wgll[ix.i[0]] * wgll[ix.i[1]];
   if constexpr (D == 3) W *= wgll[ix.i[2]];
   const double me = W * det;
   Me[idx] = me;
+  const double ms = me * scale;
+  double Ji[3][3];
+  for (int b = 0; b < D; ++b)
+    for (int a = 0; a < D; ++a) {
+      Ji[b][a] = adj[b][a] * inv;                        // dxi_b / dx_a
+      MJ[(b * D + a) * V + idx] = ms * Ji[b][a];
+    }
   int p = 0;
   for (int b = 0; b < D; ++b)
     for (int c = b; c < D; ++c) {
@@ -263,7 +266,7 @@ struct View {
   double *f, *fs, *g, *r, *rho, *mu, *lapr, *Fp;   // state and scratch
   double* drho;                                    // [D][V] reference gradient of rho (k_lap)
   int* flags;                                      // [0] setup, [1] non-finite
-  const double *Jinv, *Gm, *Me, *invMg, *Dm;      // geometry, GLL derivative matrix
+  const double *MJ, *Gm, *Me, *invMg, *Dm;        // geometry (MJ = M_e S J^-1), GLL D
   const int *off, *idx, *wslot;                    // gather-scatter CSR, wall slots
   const double *wet, *ae;                          // wall records
   const double* wub;   // [Q][R] flux bounce-back wall-velocity coefficients (or unused)
@@ -367,8 +370,7 @@ __device__ __forceinline__ void body_force(const View& v, int eb, double* sm) {
   constexpr int D = L::D, NL = ipow(NP, D), NT = EPB * NL;
   const int64_t V = v.V;
   const int E = v.E;
-  const double* __restrict__ Jinv = v.Jinv;
-  const double* __restrict__ Me = v.Me;
+  const double* __restrict__ MJ = v.MJ;
   const double* __restrict__ Dmat = v.Dm;
   double* __restrict__ Fp = v.Fp;
   double* sD = sm;
@@ -392,18 +394,18 @@ __device__ __forceinline__ void body_force(const View& v, int eb, double* sm) {
 #pragma unroll
     for (int b = 0; b < D; ++b) dr[b] = v.drho[b * V + idx];
     grad_ref<D, NP>(Dr, ix, smu + le * NL, k, dm);
-    const double rh = sr[le * NL + k];
-    const double me = __ldg(Me + idx);
+    // reference components of (c_s^2 d rho - rho d mu) / S; MJ carries M_e S
+    constexpr double kF = kCs2 / L::S, kInvS = 1.0 / L::S;
+    const double rs = sr[le * NL + k] * kInvS;
+    double w[D];
+#pragma unroll
+    for (int b = 0; b < D; ++b) w[b] = fma(kF, dr[b], -rs * dm[b]);
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-      double gr = 0.0, gm = 0.0;
+      double F = __ldg(MJ + a * V + idx) * w[0];
 #pragma unroll
-      for (int b = 0; b < D; ++b) {
-        const double j = __ldg(Jinv + (b * D + a) * V + idx);
-        gr = (b == 0) ? j * dr[b] : fma(j, dr[b], gr);
-        gm = (b == 0) ? j * dm[b] : fma(j, dm[b], gm);
-      }
-      Fp[a * V + idx] = me * fma(kCs2, gr, -rh * gm);
+      for (int b = 1; b < D; ++b) F = fma(__ldg(MJ + (b * D + a) * V + idx), w[b], F);
+      Fp[a * V + idx] = F;
     }
   }
 }
@@ -424,13 +426,16 @@ __device__ __forceinline__ void body_dss_collide(const View& v, int g) {
   const int j0 = off[g], j1 = off[g + 1];
   const int i0 = idx[j0];
   const double im = __ldg(v.invMg + g);
-  double F[D];   // gather-scatter average of M_e F_e
+  double F[D];   // gather-scatter average of M_e F_e (copy loop outermost)
 #pragma unroll
-  for (int a = 0; a < D; ++a) {
-    double s = Fp[a * V + i0];
-    for (int j = j0 + 1; j < j1; ++j) s += Fp[a * V + idx[j]];
-    F[a] = s * im;
+  for (int a = 0; a < D; ++a) F[a] = Fp[a * V + i0];
+  for (int j = j0 + 1; j < j1; ++j) {
+    const int ii = idx[j];
+#pragma unroll
+    for (int a = 0; a < D; ++a) F[a] += Fp[a * V + ii];
   }
+#pragma unroll
+  for (int a = 0; a < D; ++a) F[a] *= im;
   double fa[Q];
 #pragma unroll
   for (int q = 0; q < Q; ++q) fa[q] = f[q * V + i0];
@@ -500,8 +505,7 @@ __device__ __forceinline__ void body_rhs(const View& v, const double* __restrict
   constexpr int D = L::D, Q = L::Q, NL = ipow(NP, D), NT = EPB * NL;
   const int64_t V = v.V;
   const int E = v.E;
-  const double* __restrict__ Jinv = v.Jinv;
-  const double* __restrict__ Me = v.Me;
+  const double* __restrict__ MJ = v.MJ;
   const double* __restrict__ Dmat = v.Dm;
   const int* __restrict__ wslot = v.wslot;
   const double* __restrict__ wae = v.ae;
@@ -536,30 +540,32 @@ __device__ __forceinline__ void body_rhs(const View& v, const double* __restrict
   double vv[D];   // d_b rho - (rho / c_s^2) d_b mu, reference components
 #pragma unroll
   for (int b = 0; b < D; ++b) vv[b] = fma(-rh3, dm[b], dr[b]);
-  double J[D][D];
+  double J[D][D];   // M_e S J^-1
 #pragma unroll
   for (int b = 0; b < D; ++b)
 #pragma unroll
-    for (int a = 0; a < D; ++a) J[b][a] = __ldg(Jinv + (b * D + a) * V + idx);
-  const double ms = __ldg(Me + idx) * L::S;
+    for (int a = 0; a < D; ++a) J[b][a] = __ldg(MJ + (b * D + a) * V + idx);
   const int slot = __ldg(wslot + idx);
   static_for<0, L::NREP>([&](auto RR) {
     constexpr int A = L::rep(decltype(RR)::value), B = L::opp(A);
     constexpr double T = L::t(A);
-    double c[D];   // (J^-1 C_A)_b: e_A . grad = S sum_b c_b d_b
+    double c[D];   // (M_e S J^-1 C_A)_b: M_e e_A . grad = sum_b c_b d_b
 #pragma unroll
     for (int b = 0; b < D; ++b) c[b] = L::template cdot<A>(J[b]);
     double dA[D], dB[D];
     grad_ref2<D, NP>(Dr, ix, sg + (A - 1) * NT + lb, sg + (B - 1) * NT + lb, k, dA, dB);
-    double sA = c[0] * fma(T, vv[0], -dA[0]);
-    double sB = c[0] * fma(T, vv[0], -dB[0]);
+    // r_A = M_e (t e_A.v - e_A.grad g_A), r_B = -M_e (t e_A.v - e_A.grad g_B), e_B = -e_A
+    double cv = c[0] * vv[0];
+#pragma unroll
+    for (int b = 1; b < D; ++b) cv = fma(c[b], vv[b], cv);
+    const double tcv = T * cv;
+    double rA = fma(-c[0], dA[0], tcv);
+    double rB = fma(c[0], dB[0], -tcv);
 #pragma unroll
     for (int b = 1; b < D; ++b) {
-      sA = fma(c[b], fma(T, vv[b], -dA[b]), sA);
-      sB = fma(c[b], fma(T, vv[b], -dB[b]), sB);
+      rA = fma(-c[b], dA[b], rA);
+      rB = fma(c[b], dB[b], rB);
     }
-    double rA = ms * sA;
-    double rB = -ms * sB;
     if (slot >= 0) {
       const double gA = sg[(A - 1) * NT + lb + k], gB = sg[(B - 1) * NT + lb + k];
       rA = fma(__ldg(wae + (int64_t)A * R + slot), gA - gB, rA);
@@ -609,16 +615,21 @@ __device__ __forceinline__ void body_dss_rk(const View& v, const double* gcur, d
   const int j0 = off[g], j1 = off[g + 1];
   const int i0 = idx[j0];
   const double imdt = __ldg(v.invMg + g) * v.dt;   // dt L = dt DSS(r) / M_g
+  // DSS(r_q), summed copy by copy in the group's fixed order; the copy loop is
+  // outside the velocity loop so that each copy's Q-1 loads are independent
   double val[Q];
+  val[0] = 0.0;   // the rest population does not stream
+#pragma unroll
+  for (int q = 1; q < Q; ++q) val[q] = r[q * V + i0];
+  for (int j = j0 + 1; j < j1; ++j) {
+    const int ii = idx[j];
+#pragma unroll
+    for (int q = 1; q < Q; ++q) val[q] += r[q * V + ii];
+  }
   double rs = 0.0;
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
-    double sq = 0.0;   // DSS(r_q); the rest population does not stream
-    if (q > 0) {
-      sq = r[q * V + i0];
-      for (int j = j0 + 1; j < j1; ++j) sq += r[q * V + idx[j]];
-    }
-    val[q] = rk_update<STAGE>(q, sq, imdt, U0[q * V + i0], gcur[q * V + i0]);
+    val[q] = rk_update<STAGE>(q, val[q], imdt, U0[q * V + i0], gcur[q * V + i0]);
     rs += val[q];
   }
   if (nonfinite(rs)) atomicOr(v.flags + 1, 1);

@@ -277,8 +277,9 @@ struct Impl {
     return 0;
   }
   static void geom(sem_lbm& s) {
-    k_geom<D, NP, EPB><<<blocks(s), THREADS, SM_GEOM, s.stream>>>(s.xyz, s.Dm, s.wg, s.Jinv, s.Gm,
-                                                                  s.Me, s.flags, s.V, (int)s.E);
+    k_geom<D, NP, EPB><<<blocks(s), THREADS, SM_GEOM, s.stream>>>(s.xyz, s.Dm, s.wg, L::S, s.MJ,
+                                                                  s.Gm, s.Me, s.flags, s.V,
+                                                                  (int)s.E);
     k_dss_mass<<<grid_of(s.G, kDssThreads), kDssThreads, 0, s.stream>>>(s.off, s.idx, (int)s.G,
                                                                         s.Me, s.invMg);
   }
@@ -411,7 +412,7 @@ size_t layout(sem_lbm& s, char* base) {
   s.lapr = c.take<double>(V);
   s.Fp = c.take<double>(D * V);
   s.drho = c.take<double>(D * V);
-  s.Jinv = c.take<double>(D * D * V);
+  s.MJ = c.take<double>(D * D * V);
   s.Gm = c.take<double>(D * (D + 1) / 2 * V);
   s.Me = c.take<double>(V);
   s.invMg = c.take<double>(s.G);
@@ -441,7 +442,7 @@ void fill_view(sem_lbm& s) {
   v.f = s.f; v.fs = s.fs; v.g = s.g; v.r = s.r;
   v.rho = s.rho; v.mu = s.mu; v.lapr = s.lapr; v.Fp = s.Fp; v.drho = s.drho;
   v.flags = s.flags;
-  v.Jinv = s.Jinv; v.Gm = s.Gm; v.Me = s.Me; v.invMg = s.invMg; v.Dm = s.Dm;
+  v.MJ = s.MJ; v.Gm = s.Gm; v.Me = s.Me; v.invMg = s.invMg; v.Dm = s.Dm;
   v.off = s.off; v.idx = s.idx; v.wslot = s.slot; v.wet = s.wet; v.ae = s.ae;
   v.R = (int)s.R; v.E = (int)s.E; v.G = (int)s.G;
   v.wub = s.wub;

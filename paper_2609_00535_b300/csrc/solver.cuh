@@ -42,7 +42,7 @@ struct sem_lbm {
   bool own_ws = false;
   size_t ws_bytes = 0;
   // device arrays
-  double *f, *fs, *g, *r, *rho, *mu, *lapr, *Fp, *drho, *Jinv, *Gm, *Me, *invMg, *xyz, *Dm, *wg;
+  double *f, *fs, *g, *r, *rho, *mu, *lapr, *Fp, *drho, *MJ, *Gm, *Me, *invMg, *xyz, *Dm, *wg;
   int *off, *idx, *slot, *rec_elem, *rec_node, *rec_mask, *flags;
   double *wet, *ae, *rec_cos, *rec_ub, *wub;
   bool moving = false;   // some wall has a non-zero velocity

@@ -5,15 +5,15 @@ the method, not the instructions a compiler emits): a fused multiply-add is
 2 flops and 1 FP64 pipe operation; an add or a multiply is 1 of each.  Let
 n = N+1, d the dimension, M = Q-1 moving velocities.
 
-k_rhs (force-split streaming right-hand side, per element-local node):
+k_rhs (force-split streaming right-hand side, per element-local node; the
+metric array holds M_e S J^-1, so the mass and the speed scale cost nothing):
   reference derivatives of mu               d derivatives (those of rho are
                                             stored by k_lap of the same stage)
   v_b = d_b rho - (rho/c_s^2) d_b mu        1 mul + d fma
-  M_e * |e| scale                           1 mul
-  per velocity pair, c = J^-1 C_alpha       D2Q9: 0 (axis) or d adds (diagonal);
-                                            D3Q13: d fma
-  per moving velocity                       d derivatives, d fma (t v - dg),
-                                            1 mul + (d-1) fma (dot), 1 mul (M_e)
+  per velocity pair, c = M_e S J^-1 C_alpha D2Q9: 0 (axis) or d adds (diagonal);
+                                            D3Q13: d fma; cubic sets: (k-1) d adds
+  per velocity pair, t c.v                  1 mul + (d-1) fma, 1 mul
+  per moving velocity                       d derivatives, d fma (t c.v - c.dg)
   wall records, per moving velocity         1 sub + 1 fma
 A derivative along one axis is 1 mul + (n-1) fma.
 """
@@ -50,13 +50,14 @@ def rhs_work_per_node(lattice, N):
     n, d = N + 1, _DIM[lattice]
     M = 2 * len(_REP_NONZERO[lattice])   # moving velocities
     dv = _deriv(n)
-    ops = d * dv["ops"] + 1 + d + 1
-    flops = d * dv["flops"] + 1 + 2 * d + 1
+    ops = d * dv["ops"] + 1 + d
+    flops = d * dv["flops"] + 1 + 2 * d
     po, pf = _pair_coeff_work(lattice, d)
-    ops += po
-    flops += pf
-    per_v_ops = d * dv["ops"] + d + d + 1
-    per_v_flops = d * dv["flops"] + 2 * d + (1 + 2 * (d - 1)) + 1
+    P = M // 2
+    ops += po + P * (d + 1)
+    flops += pf + P * (2 * d - 1 + 1)
+    per_v_ops = d * dv["ops"] + d
+    per_v_flops = d * dv["flops"] + 2 * d
     return {"ops": ops + M * per_v_ops, "flops": flops + M * per_v_flops}
 
 
@@ -112,9 +113,9 @@ def step_work(lattice, N, n_local, n_groups, n_wall_nodes):
     # k_dss_mu (x3): sum of copies, 1/M, mu0 and -kappa lap
     add(10, 11, 3 * G)
     add(1, 1, 3 * X)
-    # k_force (x1): grad mu, physical gradients, M_e (c^2 grad rho - rho grad mu)
-    add(d * dv["ops"] + 2 * d * d + 3 * d,
-        d * dv["flops"] + 2 * d * (2 * d - 1) + 4 * d, V)
+    # k_force (x1): grad mu, reference (c^2 d rho - rho d mu)/S, metric M_e S J^-1
+    add(d * dv["ops"] + 1 + 2 * d + d * d,
+        d * dv["flops"] + 1 + 3 * d + d * (2 * d - 1), V)
     # k_dss_collide (x1): force average, momentum, equilibrium and F**
     cd = _cdot_ops(lattice)
     mom = sum(1 + k for k in _REP_NONZERO[lattice])            # difference + components
