@@ -100,6 +100,13 @@ typedef struct {
                              tag 0..n_tags, entering the flux bounce-back term
                              -2 t_a rho e_a.u_b / c_s^2 (Sec. 2.2); NULL = static.
                              Walls with tag < 0 are static.                          */
+  int force_split;        /* which force enters F** of the collision (Sec. 2.1):
+                             0 = F = c_s^2 grad rho - rho grad mu, as printed;
+                             1 = its potential part -rho grad mu alone.  The two
+                             have the same equilibria (F** vanishes at u = 0);
+                             with 0, long runs of isolated drops develop a growing
+                             mode whose rate per unit time falls with dt, with 1
+                             they stay bounded.  Other values: SEMLBM_EINVAL.      */
 } sem_lbm_params;
 
 typedef struct sem_lbm sem_lbm_t;

@@ -46,7 +46,8 @@ from .geometry import Mesh, deriv
 
 class Params:
     def __init__(self, rho_l=1.0, rho_v=0.1, beta=1e-3, kappa=None, delta=None, tau=0.5,
-                 dt=None, theta_w=np.pi / 2, theta_tag=(), mu0_factor=2.0, wall_velocity=None):
+                 dt=None, theta_w=np.pi / 2, theta_tag=(), mu0_factor=2.0, wall_velocity=None,
+                 force_split=0):
         self.rho_l, self.rho_v, self.beta, self.tau = rho_l, rho_v, beta, tau
         if kappa is None:
             # Appendix A: kappa = beta delta^2 (rho_l - rho_v)^2 / 8
@@ -59,6 +60,11 @@ class Params:
         self.theta_tag = tuple(theta_tag)
         self.mu0_factor = mu0_factor
         self.wall_velocity = dict(wall_velocity or {})   # tag -> u_b
+        # force entering F** of the collision: 0 = F = c_s^2 grad rho - rho grad mu
+        # as printed (Sec. 2.1); 1 = its potential part -rho grad mu alone
+        if force_split not in (0, 1):
+            raise ValueError("force_split must be 0 or 1")
+        self.force_split = force_split
 
     def u_b(self, tag, dim):
         """Velocity of the walls with this tag (zero unless given; tags < 0 are static)."""
@@ -131,9 +137,12 @@ class SemLbm:
 
     # --- forcing (Sec. 2.1) --------------------------------------------------
     def force(self, rho, mu):
-        """Nodal F = c_s^2 grad(rho) - rho grad(mu), gather-scatter averaged."""
+        """Nodal F = c_s^2 grad(rho) - rho grad(mu) (or -rho grad(mu) alone when
+        force_split = 1), gather-scatter averaged; it enters only F**."""
         m = self.mesh
-        Fe = self.cs2 * m.grad(rho) - rho[..., None] * m.grad(mu)
+        Fe = -rho[..., None] * m.grad(mu)
+        if self.p.force_split == 0:
+            Fe = self.cs2 * m.grad(rho) + Fe
         return np.stack([m.dss_average(m.Me * Fe[..., a]) for a in range(m.dim)], axis=-1)
 
     def equilibrium(self, rho, u):

@@ -273,6 +273,7 @@ struct View {
   int R, E, G, has_ub;
   int64_t V;
   double dt, omega, kappa, fbeta, rho_l, rho_v;    // omega = 1/(tau + 1/2), fbeta = mu0 factor * beta
+  double fgrad;   // 1: F** uses c_s^2 grad rho - rho grad mu; 0: -rho grad mu alone
 };
 
 // ---------------------------------------------------------------------------
@@ -394,8 +395,10 @@ __device__ __forceinline__ void body_force(const View& v, int eb, double* sm) {
 #pragma unroll
     for (int b = 0; b < D; ++b) dr[b] = v.drho[b * V + idx];
     grad_ref<D, NP>(Dr, ix, smu + le * NL, k, dm);
-    // reference components of (c_s^2 d rho - rho d mu) / S; MJ carries M_e S
-    constexpr double kF = kCs2 / L::S, kInvS = 1.0 / L::S;
+    // reference components of (c_s^2 d rho - rho d mu) / S (the first term
+    // times fgrad); MJ carries M_e S
+    constexpr double kInvS = 1.0 / L::S;
+    const double kF = (kCs2 / L::S) * v.fgrad;
     const double rs = sr[le * NL + k] * kInvS;
     double w[D];
 #pragma unroll

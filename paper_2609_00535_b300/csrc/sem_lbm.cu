@@ -454,6 +454,7 @@ void fill_view(sem_lbm& s) {
   v.fbeta = s.mu0f * s.beta;
   v.rho_l = s.rho_l;
   v.rho_v = s.rho_v;
+  v.fgrad = s.force_split ? 0.0 : 1.0;
 }
 
 int diag_blocks_for(int64_t V) { return (int)std::min<int64_t>(1184, (V + 255) / 256); }
@@ -507,6 +508,8 @@ int sem_lbm_create(const sem_lbm_mesh* mesh, int N, sem_lbm_lattice lattice, dou
     return fail(SEMLBM_EINVAL, "beta, kappa, tau must be positive and theta_w finite");
   sem_lbm_params p{};
   if (params) p = *params;
+  if (p.force_split != 0 && p.force_split != 1)
+    return fail(SEMLBM_EINVAL, "force_split must be 0 or 1 (got %d)", p.force_split);
   HostMaps h;
   if (int rc = build_maps(mesh, N, theta_w, &p, h)) return rc;
 
@@ -530,6 +533,7 @@ int sem_lbm_create(const sem_lbm_mesh* mesh, int N, sem_lbm_lattice lattice, dou
   s->rho_l = p.rho_l > 0 ? p.rho_l : 1.0;
   s->rho_v = p.rho_v > 0 ? p.rho_v : 0.1;
   s->mu0f = p.mu0_factor > 0 ? p.mu0_factor : 2.0;
+  s->force_split = p.force_split;
   const double speed = speed_max(lattice);
   if (p.dt > 0) {
     s->dt = p.dt;

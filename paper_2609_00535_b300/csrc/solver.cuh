@@ -36,6 +36,7 @@ struct sem_lbm {
   sem_lbm_lattice lat;
   int64_t E, V, G, R;
   double beta, kappa, tau, theta_w, rho_l, rho_v, dt, mu0f;
+  int force_split;   // 0: F** from c_s^2 grad rho - rho grad mu; 1: -rho grad mu
   cudaStream_t stream;
   bool own_stream = false;
   void* ws = nullptr;

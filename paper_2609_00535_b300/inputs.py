@@ -295,6 +295,7 @@ class Case:
     steps: int = 0
     extra: dict = field(default_factory=dict)
     wall_velocity: dict = field(default_factory=dict)   # wall tag -> u_b
+    force_split: int = 0   # force in F**: 0 c_s^2 grad rho - rho grad mu, 1 -rho grad mu
 
     @property
     def nodes(self):
@@ -377,7 +378,8 @@ def periodic_droplet(dim=2, ne=4, N=8, L=1.0, D=0.5, Cn=0.063, beta=1e-3, tau=0.
     lat = "D2Q9" if dim == 2 else "D3Q13"
     rho0 = droplet_density(mesh, (L / 2,) * dim, D / 2, delta, rho_l, rho_v)
     return Case("droplet%dd" % dim, mesh, lat, rho_l, rho_v, beta, kappa, tau,
-                cfl_dt(mesh, lat, cfl, kappa, rho_l), math.pi / 2, (), rho0, steps, {"delta": delta})
+                cfl_dt(mesh, lat, cfl, kappa, rho_l), math.pi / 2, (), rho0, steps,
+                {"delta": delta, "R": D / 2})
 
 
 # ---------------------------------------------------------------------------
@@ -424,7 +426,7 @@ def closed_box_drop(N=4, ne=8, R=0.25, beta=0.1, delta=0.1, tau=1.0, rho_l=1.0, 
     rho0 = droplet_density(mesh, (0.5, 0.5), R, delta, rho_l, rho_v)
     return Case("boxdrop2d", mesh, "D2Q9", rho_l, rho_v, beta, kappa, tau,
                 cfl_dt(mesh, "D2Q9", cfl, kappa, rho_l), math.pi / 2, (), rho0, 0,
-                {"delta": delta})
+                {"delta": delta, "R": R})
 
 
 def batch_mix(n=64, seed=4, elems=(256, 4096), orders=(4, 5, 6, 7, 8)):

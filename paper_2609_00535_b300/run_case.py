@@ -31,6 +31,8 @@ def make(args):
             kw["beta"] = args.beta
         if args.tau:
             kw["tau"] = args.tau
+        if args.Cn:
+            kw["Cn"] = args.Cn
         return inputs.periodic_droplet(dim=dim, ne=args.ne or 4, N=args.N or 8, cfl=args.cfl, **kw)
     raise SystemExit("unknown case " + args.case)
 
@@ -46,8 +48,12 @@ def main():
     ap.add_argument("--beta", type=float, default=None)
     ap.add_argument("--tau", type=float, default=None)
     ap.add_argument("--cfl", type=float, default=0.4)
+    ap.add_argument("--Cn", type=float, default=None, help="interface width / diameter (droplets)")
+    ap.add_argument("--force-split", type=int, default=0,
+                    help="force in F**: 0 c_s^2 grad rho - rho grad mu, 1 -rho grad mu")
     args = ap.parse_args()
     case = make(args)
+    case.force_split = args.force_split
     s = semlbm.Solver.from_case(case)
     s.set_density(case.rho0)
     out, done = [], 0
@@ -60,7 +66,14 @@ def main():
         if d["status"] != 0 or not d["ke_max"] < 1.0:
             break
     wall = time.perf_counter() - t0
+    # viscous time t_eta = eta D / gamma and La = gamma D / eta^2 (Sec. 3.3), with
+    # eta = rho_l nu and nu = tau c_s^2 dt; D the drop diameter (or 2R)
+    gamma = (case.rho_l - case.rho_v) ** 3 * math.sqrt(2 * case.kappa * case.beta) / 6
+    eta = case.rho_l * case.tau * case.dt / 3.0
+    D = 2 * case.extra.get("R", 0.25)
     print(json.dumps({"case": case.name, "nodes": case.nodes, "dt": case.dt, "tau": case.tau,
+                      "force_split": case.force_split, "La": gamma * D / eta ** 2,
+                      "T_over_t_eta": done * case.dt * gamma / (eta * D),
                       "steps": done, "us_per_step": 1e6 * wall / done,
                       "ke_max": ["%d:%.2e" % x for x in out[:: max(1, len(out) // 12)]]
                       + ["%d:%.2e" % out[-1]]}))

@@ -50,7 +50,8 @@ class ParamsC(ctypes.Structure):
                 ("cfl", ctypes.c_double), ("mu0_factor", ctypes.c_double),
                 ("n_tags", ctypes.c_int), ("theta_tag", ctypes.c_void_p),
                 ("stream", ctypes.c_void_p), ("workspace", ctypes.c_void_p),
-                ("workspace_bytes", ctypes.c_size_t), ("wall_velocity", ctypes.c_void_p)]
+                ("workspace_bytes", ctypes.c_size_t), ("wall_velocity", ctypes.c_void_p),
+                ("force_split", ctypes.c_int)]
 
 
 class DiagC(ctypes.Structure):
@@ -183,7 +184,7 @@ class Solver:
 
     def __init__(self, mesh, lattice, beta, kappa, tau, theta_w, theta_tag=(), rho_l=1.0,
                  rho_v=0.1, dt=0.0, cfl=0.0, mu0_factor=0.0, stream=None, device=0,
-                 wall_velocity=None):
+                 wall_velocity=None, force_split=0):
         import torch
         L = load()
         self.lattice = LATTICES.get(lattice, lattice)
@@ -208,7 +209,7 @@ class Solver:
         p = ParamsC(rho_l, rho_v, dt, cfl, mu0_factor, len(self._tags),
                     self._tags.ctypes.data if len(self._tags) else None,
                     self.stream.cuda_stream, self.workspace.data_ptr(), nbytes,
-                    self._ub.ctypes.data if self._ub is not None else None)
+                    self._ub.ctypes.data if self._ub is not None else None, int(force_split))
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             check(L.sem_lbm_create(ctypes.byref(m), self.N, self.lattice, beta, kappa, tau,
@@ -219,9 +220,10 @@ class Solver:
 
     @classmethod
     def from_case(cls, case, **kw):
+        kw.setdefault("wall_velocity", getattr(case, "wall_velocity", None))
+        kw.setdefault("force_split", getattr(case, "force_split", 0))
         return cls(case.mesh, case.lattice, case.beta, case.kappa, case.tau, case.theta_w,
-                   case.theta_tag, case.rho_l, case.rho_v, dt=case.dt,
-                   wall_velocity=getattr(case, "wall_velocity", None), **kw)
+                   case.theta_tag, case.rho_l, case.rho_v, dt=case.dt, **kw)
 
     # -- state -------------------------------------------------------------
     def set_density(self, rho):

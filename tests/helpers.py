@@ -14,7 +14,7 @@ def oracle_of(case, **over):
     lat = lattice.by_name(case.lattice)
     kw = dict(rho_l=case.rho_l, rho_v=case.rho_v, beta=case.beta, kappa=case.kappa,
               tau=case.tau, dt=case.dt, theta_w=case.theta_w, theta_tag=case.theta_tag,
-              wall_velocity=case.wall_velocity)
+              wall_velocity=case.wall_velocity, force_split=case.force_split)
     kw.update(over)
     return om, method.SemLbm(om, lat, method.Params(**kw))
 

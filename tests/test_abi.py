@@ -81,3 +81,37 @@ def test_workspace_bytes_is_host_only_and_scales():
     V = 16 * 25
     assert b2 > 4 * 9 * V * 8
     assert semlbm.workspace_bytes(inputs.box((2, 2), (0, 0), (1, 1), 4), 4, "D3Q13") == 0
+
+
+STRUCTS = [("sem_lbm_mesh", semlbm.MeshC), ("sem_lbm_params", semlbm.ParamsC),
+           ("sem_lbm_diag", semlbm.DiagC), ("sem_lbm_profile_t", semlbm.ProfileC),
+           ("sem_lbm_info_t", semlbm.InfoC), ("sem_lbm_batch_group_info", semlbm.GroupInfoC)]
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Every ctypes mirror has the size and field offsets the C compiler gives
+    the header's struct (guards the binding when the ABI grows)."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "sem_lbm.h"', 'int main(void) {']
+    for cname, py in STRUCTS:
+        lines.append('printf("%s size %%zu\\n", sizeof(%s));' % (cname, cname))
+        for fname, _ in py._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (cname, fname, cname, fname))
+    lines += ['return 0;', '}']
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n"):
+        if line:
+            a, b, v = line.split()
+            got[(a, b)] = int(v)
+    for cname, py in STRUCTS:
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)

@@ -214,3 +214,26 @@ def test_couette_profile_on_gpu():
     y = m.node_xyz[..., 1].reshape(-1)
     assert np.abs(u[0] - U * y / H).max() < 1e-4 * U
     s.close()
+
+
+@pytest.mark.parametrize("kind", ["droplet2d", "flat2d", "sphere3d"])
+def test_force_split_potential_part(kind):
+    """force_split = 1 (F** from -rho grad mu alone) against the oracle's same reading."""
+    if kind == "droplet2d":
+        case = inputs.periodic_droplet(dim=2, ne=4, N=6, Cn=0.25)
+        steps = 150
+    elif kind == "flat2d":
+        case = inputs.flat_wall_2d()
+        steps = 200
+    else:
+        case = inputs.sphere_3d(N=3, ne=(3, 3, 2))
+        steps = 40
+    case.force_split = 1
+    _compare(case, steps)
+
+
+def test_force_split_rejects_other_values():
+    from paper_2609_00535_b300 import semlbm
+    case = inputs.flat_wall_2d()
+    with pytest.raises(semlbm.SemLbmError):
+        semlbm.Solver.from_case(case, force_split=2)

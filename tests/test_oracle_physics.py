@@ -162,3 +162,32 @@ def test_couette_flow_between_a_static_and_a_sliding_wall():
     assert np.abs(u[:, 0] - U * y / H).max() < 2e-3 * U
     assert np.abs(u[:, 1]).max() < 1e-6 * U
     assert abs(s.diagnostics(f)["mass"] - s.diagnostics(s.initial_state(c.rho0.reshape(om.shape)))["mass"]) < 1e-13
+
+
+@pytest.mark.parametrize("force_split", [0, 1])
+def test_collision_force_second_moment(force_split):
+    """Sec. 2.1: for f = f^eq(rho, u) the collision adds dt (1 - omega/2) F**,
+    whose second moment is u F + F u (Guo's second-order forcing term), with
+    F = c_s^2 grad rho - rho grad mu (force_split 0) or -rho grad mu (1).  On an
+    affine mesh with linear rho and mu both gradients are exact, so F is known
+    in closed form at every node."""
+    m = inputs.box((3, 2), (0, 0), (1.5, 1.0), 4)
+    c = make_case("fss", m, "D2Q9", 1e-3, 0.1, 0.8, math.pi / 2,
+                  rho0=np.ones(m.global_id.shape))
+    c.force_split = force_split
+    om, s = oracle_of(c)
+    x = m.node_xyz.reshape(om.shape + (2,))
+    b, a = np.array([0.03, -0.02]), np.array([0.5, 0.25])      # grad rho, grad mu
+    rho = 0.6 + x @ b
+    mu = 0.1 + x @ a
+    u = np.broadcast_to(np.array([2e-3, -1e-3]), rho.shape + (2,))
+    f = s.equilibrium(rho, u)
+    fs = s.collide(f, rho, mu)
+    omega = 1.0 / (c.tau + 0.5)
+    src = (fs - f) / (c.dt * (1 - 0.5 * omega))
+    F = (-rho[..., None] * a) + (s.cs2 * b if force_split == 0 else 0.0)
+    mom2 = np.einsum("q...,qi,qj->...ij", src, s.lat.e, s.lat.e)
+    want = u[..., :, None] * F[..., None, :] + F[..., :, None] * u[..., None, :]
+    np.testing.assert_allclose(mom2, want, atol=1e-13)
+    np.testing.assert_allclose(src.sum(0), 0.0, atol=1e-14)
+    np.testing.assert_allclose(np.einsum("q...,qi->...i", src, s.lat.e), 0.0, atol=1e-14)
