@@ -162,6 +162,26 @@ int sem_lbm_step(sem_lbm_t* s, int64_t n_steps);
 /* Reduce the diagnostics of the current state (synchronises the stream). */
 int sem_lbm_diagnostics(sem_lbm_t* s, sem_lbm_diag* out);
 
+/* Moments of the liquid fraction phi = (rho - rho_v)/(rho_l - rho_v) of the
+ * current state, from which the static contact angle of a drop is measured
+ * (Sec. 3.1 and 3.2 measure it on the equilibrium cap; the paper states no
+ * procedure).  On a flat wall the cap's liquid volume and wetted base give the
+ * angle (paper_2609_00535_b300/wetting.py).  Volume integrals use the GLL mass
+ * quadrature, wall integrals the face quadrature w |a| of the wetting term. */
+typedef struct {
+  double volume;          /* int phi dV (an area in 2D)                              */
+  double centroid[3];     /* int phi x dV / volume (components >= dim are 0)          */
+  double wall;            /* int dS over the selected wall faces (a length in 2D)     */
+  double wetted;          /* int phi dS over the selected wall faces                  */
+  double wet_centroid[3]; /* int phi x dS / wetted (0 when wetted == 0)               */
+} sem_lbm_wetting;
+
+/* tag >= 0 selects the wall faces with that tag, tag < 0 every wall face.  Runs
+ * two kernels on the solver's stream and synchronises it; the reduction order
+ * is fixed, so repeated calls give the same bits.  Errors: SEMLBM_EINVAL (NULL
+ * argument, state not set), SEMLBM_ECUDA. */
+int sem_lbm_wetting_moments(sem_lbm_t* s, int tag, sem_lbm_wetting* out);
+
 /* Copy a field out.  which: 0 fbar [Q][E][n^d], 1 rho [E][n^d],
  * 2 u [dim][E][n^d], 3 mu [E][n^d] (of the last computed stage-1 state).
  * dst is host memory unless dst_on_device; host copies synchronise. */

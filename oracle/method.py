@@ -231,6 +231,30 @@ class SemLbm:
         """fbar = f^eq(rho, u = 0) (u = 0 makes F** vanish)."""
         return self.equilibrium(rho, np.zeros(rho.shape + (self.mesh.dim,)))
 
+    def wetting_moments(self, f, tag=0):
+        """Integrals for measuring the static contact angle of Sec. 3.1 / 3.2 from
+        the state: with the liquid fraction phi = (rho - rho_v)/(rho_l - rho_v),
+        volume = int phi dV, centroid = int phi x dV / volume, and over the wall
+        faces of the given tag (all walls for tag < 0), wall = int dS,
+        wetted = int phi dS, wet_centroid = int phi x dS / wetted.  The volume
+        integral uses the GLL quadrature of the mass matrix, the wall integrals
+        the face quadrature of the wetting term (weight w |a| per face-node)."""
+        m, p = self.mesh, self.p
+        rho = self.density(f)
+        phi = (rho - p.rho_v) / (p.rho_l - p.rho_v)
+        X = m.X
+        vol = float(np.sum(m.Me * phi))
+        cen = [float(np.sum(m.Me * phi * X[..., a])) / vol for a in range(m.dim)]
+        sel = (m.wall_tag == tag) if tag >= 0 else np.ones(len(m.wall_tag), dtype=bool)
+        ws = np.linalg.norm(m.wall_area, axis=-1)[sel]
+        phw = m.at_wall(phi)[sel]
+        wall = float(np.sum(ws))
+        wet = float(np.sum(ws * phw))
+        wcen = [float(np.sum(ws * phw * m.at_wall(X[..., a])[sel])) / wet if wet else 0.0
+                for a in range(m.dim)]
+        return {"volume": vol, "centroid": cen, "wall": wall, "wetted": wet,
+                "wet_centroid": wcen}
+
     def diagnostics(self, f):
         rho = self.density(f)
         u = self.velocity(f, rho)

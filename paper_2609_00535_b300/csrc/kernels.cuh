@@ -190,7 +190,8 @@ __global__ void k_wall_setup(const double* __restrict__ xyz, const double* __res
                              const int* __restrict__ rec_node, const double* __restrict__ rec_cos,
                              const int* __restrict__ rec_mask, int R, double sq2bk,
                              const double* __restrict__ rec_ub, double* __restrict__ wet,
-                             double* __restrict__ ae, double* __restrict__ wub) {
+                             double* __restrict__ ae, double* __restrict__ wub,
+                             double* __restrict__ wsf) {
   constexpr int D = L::D, NL = ipow(NP, D);
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= R) return;
@@ -222,7 +223,10 @@ __global__ void k_wall_setup(const double* __restrict__ xyz, const double* __res
   double acc[L::Q], accu[L::Q];
   for (int q = 0; q < L::Q; ++q) acc[q] = accu[q] = 0.0;
   for (int f = 0; f < 2 * D; ++f) {
-    if (!((mask >> f) & 1)) continue;
+    if (!((mask >> f) & 1)) {
+      wsf[r * 2 * D + f] = 0.0;
+      continue;
+    }
     const int b = f >> 1;
     const double sgn = (f & 1) ? 1.0 : -1.0;
     double wf = 1.0;
@@ -234,6 +238,7 @@ __global__ void k_wall_setup(const double* __restrict__ xyz, const double* __res
       an += a[c] * a[c];
     }
     an = sqrt(an);
+    wsf[r * 2 * D + f] = an;   // face quadrature weight w |a| of this face-node
     wsum += an * rec_cos[r * 2 * D + f] * sq2bk;
     for (int q = 1; q < L::Q; ++q) {
       double dot = 0.0;
@@ -842,6 +847,84 @@ static __global__ void k_diag_final(const DiagPart* __restrict__ part, int n, Di
     a.rho_min = fmin(a.rho_min, b.rho_min);
     a.rho_max = fmax(a.rho_max, b.rho_max);
     a.nonfinite += b.nonfinite;
+  }
+  *out = a;
+}
+
+// ---------------------------------------------------------------------------
+// contact-angle measurement (Sec. 3.1, 3.2): moments of the liquid fraction
+// phi = (rho - rho_v)/(rho_l - rho_v) over the domain (GLL mass quadrature; the
+// copies of a shared node together carry its assembled mass) and over the wall
+// faces of one tag (face quadrature w |a|); per-block partials combined in a
+// fixed order, so the result does not depend on scheduling
+// ---------------------------------------------------------------------------
+struct WetPart {
+  double vol, vx[3], wall, wet, wx[3];
+};
+
+template <class L>
+__global__ void k_wet(const double* __restrict__ f, const double* __restrict__ Me,
+                      const double* __restrict__ xyz, const int* __restrict__ rec_elem,
+                      const int* __restrict__ rec_node, const int* __restrict__ rec_mask,
+                      const int* __restrict__ rec_tag, const double* __restrict__ wsf, int R,
+                      int tag, int NL, double rho_v, double inv_drho, WetPart* __restrict__ part,
+                      int64_t V) {
+  constexpr int D = L::D, Q = L::Q;
+  __shared__ WetPart sh[256];
+  WetPart p = {};
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < V; i += stride) {
+    double rh = 0.0;
+    for (int q = 0; q < Q; ++q) rh += f[q * V + i];
+    const double m = Me[i] * ((rh - rho_v) * inv_drho);
+    p.vol += m;
+    for (int c = 0; c < D; ++c) p.vx[c] += m * xyz[i * D + c];
+  }
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < R; r += stride) {
+    const int64_t i = (int64_t)rec_elem[r] * NL + rec_node[r];
+    const int mask = rec_mask[r];
+    double rh = 0.0;
+    for (int q = 0; q < Q; ++q) rh += f[q * V + i];
+    const double phi = (rh - rho_v) * inv_drho;
+    for (int fc = 0; fc < 2 * D; ++fc) {
+      if (!((mask >> fc) & 1) || (tag >= 0 && rec_tag[r * 2 * D + fc] != tag)) continue;
+      const double w = wsf[r * 2 * D + fc];
+      p.wall += w;
+      p.wet += w * phi;
+      for (int c = 0; c < D; ++c) p.wx[c] += w * phi * xyz[i * D + c];
+    }
+  }
+  sh[threadIdx.x] = p;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      WetPart& a = sh[threadIdx.x];
+      const WetPart& b = sh[threadIdx.x + s];
+      a.vol += b.vol;
+      a.wall += b.wall;
+      a.wet += b.wet;
+      for (int c = 0; c < 3; ++c) {
+        a.vx[c] += b.vx[c];
+        a.wx[c] += b.wx[c];
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+static __global__ void k_wet_final(const WetPart* __restrict__ part, int n, WetPart* __restrict__ out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  WetPart a = part[0];
+  for (int i = 1; i < n; ++i) {
+    const WetPart& b = part[i];
+    a.vol += b.vol;
+    a.wall += b.wall;
+    a.wet += b.wet;
+    for (int c = 0; c < 3; ++c) {
+      a.vx[c] += b.vx[c];
+      a.wx[c] += b.wx[c];
+    }
   }
   *out = a;
 }

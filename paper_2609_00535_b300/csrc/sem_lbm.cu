@@ -90,6 +90,7 @@ struct HostMaps {
   std::vector<int> slot;              // [V] wall record or -1
   std::vector<int> rec_elem, rec_node, rec_mask;
   std::vector<double> rec_cos;        // [R][2D]
+  std::vector<int> rec_tag;           // [R][2D] wall tag of each face (-1 if not a wall face)
   std::vector<double> rec_ub;         // [R][2D][D] wall velocity of each face (moving walls)
   bool moving = false;
   int64_t G = 0;
@@ -171,6 +172,8 @@ int build_maps(const sem_lbm_mesh* m, int N, double theta_w, const sem_lbm_param
       h.rec_node.push_back(k);
       h.rec_mask.push_back(mask[k]);
       for (int f = 0; f < 2 * D; ++f) h.rec_cos.push_back(cosf[f]);
+      for (int f = 0; f < 2 * D; ++f)
+        h.rec_tag.push_back(m->face_kind[e * 2 * D + f] == 1 ? m->face_tag[e * 2 * D + f] : -1);
       h.rec_ub.insert(h.rec_ub.end(), ubf.begin(), ubf.end());
     }
   }
@@ -288,7 +291,7 @@ struct Impl {
     k_wall_setup<L, NP><<<grid_of(s.R, 128), 128, 0, s.stream>>>(
         s.xyz, s.Dm, s.wg, s.rec_elem, s.rec_node, s.rec_cos, s.rec_mask, (int)s.R,
         std::sqrt(2.0 * s.beta / s.kappa), s.moving ? s.rec_ub : nullptr, s.wet, s.ae,
-        s.moving ? s.wub : nullptr);
+        s.moving ? s.wub : nullptr, s.wsf);
   }
   static void lap(sem_lbm& s) {
     k_lap<L, NP, EPB><<<blocks(s), THREADS, SM_LAP, s.stream>>>(s.view, s.rho, s.lapr, s.drho);
@@ -318,6 +321,12 @@ struct Impl {
     k_diag<L><<<s.diag_blocks, 256, 0, s.stream>>>(s.f, s.Me, s.parts, s.V);
     k_diag_final<<<1, 32, 0, s.stream>>>(s.parts, s.diag_blocks, s.dout);
   }
+  static void wet(sem_lbm& s, int tag) {
+    k_wet<L><<<s.diag_blocks, 256, 0, s.stream>>>(
+        s.f, s.Me, s.xyz, s.rec_elem, s.rec_node, s.rec_mask, s.rec_tag, s.wsf, (int)s.R, tag,
+        (int)s.NL, s.rho_v, 1.0 / (s.rho_l - s.rho_v), s.wparts, s.V);
+    k_wet_final<<<1, 32, 0, s.stream>>>(s.wparts, s.diag_blocks, s.wout);
+  }
   static void init(sem_lbm& s, const double* rho_in) {
     k_init<L><<<grid_of(s.V, 256), 256, 0, s.stream>>>(rho_in, s.f, s.rho, s.V);
   }
@@ -336,7 +345,7 @@ struct Impl {
   }
   static Ops* ops() {
     static Ops o{geom, wallsetup, lap, mu, force, rhs, collide, rk, diag, init, density, velocity, prepare,
-                 lap_into, mu_from};
+                 lap_into, mu_from, wet};
     return &o;
   }
 };
@@ -434,6 +443,10 @@ size_t layout(sem_lbm& s, char* base) {
   s.flags = c.take<int>(8);
   s.parts = c.take<DiagPart>(s.diag_blocks);
   s.dout = c.take<DiagPart>(1);
+  s.rec_tag = c.take<int>(R * 2 * D);
+  s.wsf = c.take<double>(R * 2 * D);
+  s.wparts = c.take<WetPart>(s.diag_blocks);
+  s.wout = c.take<WetPart>(1);
   return c.off;
 }
 
@@ -597,7 +610,8 @@ int sem_lbm_create(const sem_lbm_mesh* mesh, int N, sem_lbm_lattice lattice, dou
          up(s->rec_elem, h.rec_elem.data(), sizeof(int) * s->R) &&
          up(s->rec_node, h.rec_node.data(), sizeof(int) * s->R) &&
          up(s->rec_mask, h.rec_mask.data(), sizeof(int) * s->R) &&
-         up(s->rec_cos, h.rec_cos.data(), sizeof(double) * s->R * 2 * D);
+         up(s->rec_cos, h.rec_cos.data(), sizeof(double) * s->R * 2 * D) &&
+         up(s->rec_tag, h.rec_tag.data(), sizeof(int) * s->R * 2 * D);
   if (!ok) return bail(fail(SEMLBM_ECUDA, "upload failed: %s", cudaGetErrorString(cudaGetLastError())));
   s->ops->geom(*s);
   s->ops->wall(*s);
@@ -683,6 +697,25 @@ int sem_lbm_diagnostics(sem_lbm_t* s, sem_lbm_diag* out) {
   out->rho_max = d.rho_max;
   out->n_nonfinite = (int64_t)d.nonfinite;
   out->status = (d.nonfinite > 0 || flags[1]) ? SEMLBM_ENONFINITE : SEMLBM_OK;
+  return 0;
+}
+
+int sem_lbm_wetting_moments(sem_lbm_t* s, int tag, sem_lbm_wetting* out) {
+  if (!s || !out) return fail(SEMLBM_EINVAL, "NULL argument");
+  if (!s->state_ready) return fail(SEMLBM_EINVAL, "state not set");
+  s->ops->wet(*s, tag);
+  CUDA_TRY(cudaGetLastError());
+  WetPart w;
+  CUDA_TRY(cudaMemcpyAsync(&w, s->wout, sizeof w, cudaMemcpyDeviceToHost, s->stream));
+  CUDA_TRY(cudaStreamSynchronize(s->stream));
+  *out = sem_lbm_wetting{};
+  out->volume = w.vol;
+  out->wall = w.wall;
+  out->wetted = w.wet;
+  for (int c = 0; c < s->D; ++c) {
+    out->centroid[c] = w.vol != 0.0 ? w.vx[c] / w.vol : 0.0;
+    out->wet_centroid[c] = w.wet != 0.0 ? w.wx[c] / w.wet : 0.0;
+  }
   return 0;
 }
 

@@ -46,6 +46,9 @@ struct sem_lbm {
   double *f, *fs, *g, *r, *rho, *mu, *lapr, *Fp, *drho, *MJ, *Gm, *Me, *invMg, *xyz, *Dm, *wg;
   int *off, *idx, *slot, *rec_elem, *rec_node, *rec_mask, *flags;
   double *wet, *ae, *rec_cos, *rec_ub, *wub;
+  int* rec_tag;                         // [R][2D] wall tag per face (-1: not a wall face)
+  double* wsf;                          // [R][2D] face quadrature weight w |a|
+  semlbm::WetPart *wparts, *wout;       // wetting-moment partials
   bool moving = false;   // some wall has a non-zero velocity
   semlbm::DiagPart *parts, *dout;
   int diag_blocks = 0;
@@ -79,5 +82,6 @@ struct Ops {
   int (*prepare)();
   void (*lap_into)(sem_lbm&, const double* rho, double* partial);
   void (*mu_from)(sem_lbm&, const double* partial, const double* rho, double* mu);
+  void (*wet)(sem_lbm&, int tag);
 };
 

@@ -500,6 +500,17 @@ def sessile_cap_density(mesh, x_c, area, theta, delta, rho_l=1.0, rho_v=0.1):
     return tanh_profile(dist, delta, rho_l, rho_v)
 
 
+def sessile_cap_density_3d(mesh, x_c, y_c, volume, theta, delta, rho_l=1.0, rho_v=0.1):
+    """3D drop on the wall z = 0 at its equilibrium shape: a sphere of radius R
+    centred at (x_c, y_c, -R cos(theta)) holding `volume` above the wall,
+    V = pi R^3 (1 - cos theta)^2 (2 + cos theta) / 3."""
+    c0 = math.cos(theta)
+    R = (3 * volume / (math.pi * (1 - c0) ** 2 * (2 + c0))) ** (1.0 / 3.0)
+    c = np.array([x_c, y_c, -R * c0])
+    dist = np.sqrt(((mesh.node_xyz - c) ** 2).sum(-1)) - R
+    return tanh_profile(dist, delta, rho_l, rho_v)
+
+
 def cylinder_cap_density(mesh, center, Rc, Rd, theta, delta, rho_l=1.0, rho_v=0.1):
     """Drop of radius Rd on a cylinder of radius Rc at its equilibrium position:
     centre distance d with d^2 = Rc^2 + Rd^2 - 2 Rc Rd cos(theta), along +y."""

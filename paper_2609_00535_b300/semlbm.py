@@ -22,7 +22,7 @@ ERRORS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENONFINITE", -5
           -6: "EUNSUPPORTED"}
 
 EXPORTED = ["sem_lbm_workspace_bytes", "sem_lbm_create", "sem_lbm_set_density", "sem_lbm_step",
-            "sem_lbm_diagnostics", "sem_lbm_get_field", "sem_lbm_get_state", "sem_lbm_set_state",
+            "sem_lbm_diagnostics", "sem_lbm_wetting_moments", "sem_lbm_get_field", "sem_lbm_get_state", "sem_lbm_set_state",
             "sem_lbm_get_info", "sem_lbm_destroy", "sem_lbm_last_error", "sem_lbm_profile",
             "sem_lbm_profile_read", "sem_lbm_chemical_potential_noalloc",
             "sem_lbm_batch_create", "sem_lbm_batch_add", "sem_lbm_batch_remove",
@@ -52,6 +52,12 @@ class ParamsC(ctypes.Structure):
                 ("stream", ctypes.c_void_p), ("workspace", ctypes.c_void_p),
                 ("workspace_bytes", ctypes.c_size_t), ("wall_velocity", ctypes.c_void_p),
                 ("force_split", ctypes.c_int)]
+
+
+class WettingC(ctypes.Structure):
+    _fields_ = [("volume", ctypes.c_double), ("centroid", ctypes.c_double * 3),
+                ("wall", ctypes.c_double), ("wetted", ctypes.c_double),
+                ("wet_centroid", ctypes.c_double * 3)]
 
 
 class DiagC(ctypes.Structure):
@@ -106,6 +112,7 @@ def load():
     L.sem_lbm_set_density.argtypes = [P, P, I]
     L.sem_lbm_step.argtypes = [P, I64]
     L.sem_lbm_diagnostics.argtypes = [P, ctypes.POINTER(DiagC)]
+    L.sem_lbm_wetting_moments.argtypes = [P, I, ctypes.POINTER(WettingC)]
     L.sem_lbm_get_field.argtypes = [P, I, P, I]
     L.sem_lbm_get_state.argtypes = [P, P, I, ctypes.POINTER(I64)]
     L.sem_lbm_set_state.argtypes = [P, P, I, I64]
@@ -259,6 +266,14 @@ class Solver:
         d = DiagC()
         check(load().sem_lbm_diagnostics(self.h, ctypes.byref(d)))
         return {k: getattr(d, k) for k, _ in DiagC._fields_}
+
+    def wetting_moments(self, tag=0):
+        """Liquid-fraction moments of the current state (sem_lbm_wetting_moments):
+        volume, centroid, wall, wetted, wet_centroid; tag < 0 = every wall."""
+        w = WettingC()
+        check(load().sem_lbm_wetting_moments(self.h, int(tag), ctypes.byref(w)))
+        return {"volume": w.volume, "centroid": list(w.centroid)[:self.dim], "wall": w.wall,
+                "wetted": w.wetted, "wet_centroid": list(w.wet_centroid)[:self.dim]}
 
     def field(self, which, out=None):
         """which: 'fbar' [Q,V], 'rho' [V], 'u' [dim,V], 'mu' [V]; numpy, or into a CUDA tensor."""

@@ -1,0 +1,73 @@
+"""Static contact angle of a sessile drop on a flat wall from the wetting moments
+that the library integrates on the device (sem_lbm_wetting_moments).
+
+A drop at equilibrium on a flat wall is a circular cap (2D) or a spherical cap
+(3D) meeting the wall at the contact angle theta measured through the liquid
+(Sec. 3.1).  The moments give the cap's size two ways: the liquid area/volume
+int phi dV and the wetted wall measure int_wall phi dS (the cap's base: length
+2b in 2D, area pi b^2 in 3D).  Their scale-free ratio is a monotone function of
+theta alone, inverted here by bisection:
+
+  2D  area / b^2      = (theta - sin theta cos theta) / sin^2 theta
+  3D  V / A_w^(3/2)   = (1 - cos theta)^2 (2 + cos theta) / (3 sqrt(pi) sin^3 theta)
+
+Diffuse interfaces: for the tanh profile of width delta (Appendix A) the
+liquid fraction phi = 1/(1 + exp(4 s / delta)) (s the signed distance) integrates
+across a curved interface to the sharp value plus (pi^2/6)(delta/4)^2 times the
+integral of the summed principal curvatures over the interface (the Sommerfeld
+expansion; no odd terms, since phi - 1/2 is odd in s).  For a cap of radius R
+that adds pi^2 delta^2 theta / 48 to the 2D area, pi^3 delta^2 R (1 - cos theta) / 24
+to the 3D volume, and pi^3 (delta / sin theta)^2 / 48 to the 3D wetted area (the
+contact circle, crossed at angle theta); the 2D wetted length has no correction.
+With delta > 0 these are removed by a fixed-point iteration.
+"""
+import math
+
+
+def _bisect(fn, target, lo=1e-9, hi=math.pi - 1e-9, iters=200):
+    """theta in (lo, hi) with fn(theta) = target, fn increasing."""
+    for _ in range(iters):
+        mid = 0.5 * (lo + hi)
+        if fn(mid) < target:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
+def _g2(t):
+    return (t - math.sin(t) * math.cos(t)) / math.sin(t) ** 2
+
+
+def _g3(t):
+    c, s = math.cos(t), math.sin(t)
+    return (1 - c) ** 2 * (2 + c) / (3 * math.sqrt(math.pi) * s ** 3)
+
+
+def cap_angle_2d(area, wetted, delta=0.0, iters=20):
+    """Contact angle (radians) of a 2D circular cap from its liquid area and its
+    wetted wall length 2b."""
+    b = 0.5 * wetted
+    theta = _bisect(_g2, area / b ** 2)
+    for _ in range(iters if delta > 0 else 0):
+        theta = _bisect(_g2, (area - math.pi ** 2 * delta ** 2 * theta / 48) / b ** 2)
+    return theta
+
+
+def cap_angle_3d(volume, wetted, delta=0.0, iters=20):
+    """Contact angle (radians) of a 3D spherical cap from its liquid volume and its
+    wetted wall area pi b^2."""
+    theta = _bisect(_g3, volume / wetted ** 1.5)
+    for _ in range(iters if delta > 0 else 0):
+        s = math.sin(theta)
+        aw = wetted - math.pi ** 3 * (delta / s) ** 2 / 48
+        R = math.sqrt(aw / math.pi) / s
+        v = volume - math.pi ** 3 * delta ** 2 * R * (1 - math.cos(theta)) / 24
+        theta = _bisect(_g3, v / aw ** 1.5)
+    return theta
+
+
+def contact_angle(moments, dim, delta=0.0):
+    """Degrees; moments as returned by Solver.wetting_moments (flat wall)."""
+    f = cap_angle_2d if dim == 2 else cap_angle_3d
+    return math.degrees(f(moments["volume"], moments["wetted"], delta))

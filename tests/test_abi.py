@@ -85,7 +85,8 @@ def test_workspace_bytes_is_host_only_and_scales():
 
 STRUCTS = [("sem_lbm_mesh", semlbm.MeshC), ("sem_lbm_params", semlbm.ParamsC),
            ("sem_lbm_diag", semlbm.DiagC), ("sem_lbm_profile_t", semlbm.ProfileC),
-           ("sem_lbm_info_t", semlbm.InfoC), ("sem_lbm_batch_group_info", semlbm.GroupInfoC)]
+           ("sem_lbm_info_t", semlbm.InfoC), ("sem_lbm_batch_group_info", semlbm.GroupInfoC),
+           ("sem_lbm_wetting", semlbm.WettingC)]
 
 
 def test_binding_structs_match_the_header(tmp_path):

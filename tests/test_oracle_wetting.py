@@ -1,0 +1,89 @@
+"""Pins of the oracle's wetting moments and of the contact-angle inversion.
+
+The liquid fraction of the tanh profile (Appendix A) is the Fermi function
+phi = 1/(1 + exp(4 s / delta)) of the signed distance s, whose integrals across
+a curved interface follow the Sommerfeld expansion with no odd terms:
+  disc of radius R:      int phi dA = pi R^2 + pi^3 delta^2 / 48
+  ball of radius R:      int phi dV = 4 pi R^3 / 3 + pi^3 delta^2 R / 12
+  a line through a disc: int phi dx = 2 R   (exactly, up to exp(-4R/delta) terms)
+Halves of these sit on a wall through the centre.  The oracle's quadratures
+converge to them spectrally; the contact-angle inversion recovers sharp caps
+exactly and the equilibrium-cap initial densities to within two degrees.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2609_00535_b300 import inputs, wetting
+from tests.helpers import make_case, oracle_of
+
+
+def _moments(mesh, lattice, rho0, tag=0):
+    c = make_case("w", mesh, lattice, 1e-3, 0.1, 0.5, math.pi / 2, theta_tag=(math.pi / 2,),
+                  rho0=rho0)
+    om, o = oracle_of(c)
+    return o.wetting_moments(o.initial_state(rho0.reshape(om.shape)), tag)
+
+
+def test_half_disc_on_a_wall():
+    R, d = 0.4, 0.1
+    m = inputs.box((16, 8), (0, 0), (2, 1), 8, face_tags={2: 0})
+    rho0 = inputs.tanh_profile(np.sqrt(((m.node_xyz - [1.0, 0.0]) ** 2).sum(-1)) - R, d, 1.0, 0.1)
+    w = _moments(m, "D2Q9", rho0)
+    assert w["volume"] == pytest.approx(0.5 * math.pi * (R * R + math.pi ** 2 * d * d / 48), rel=1e-7)
+    assert w["wetted"] == pytest.approx(2 * R, rel=1e-7)
+    assert w["wall"] == pytest.approx(2.0, rel=1e-13)              # the tag-0 wall y = 0
+    assert w["wet_centroid"][0] == pytest.approx(1.0, abs=1e-12)
+    assert w["centroid"][0] == pytest.approx(1.0, abs=1e-12)
+    every = _moments(m, "D2Q9", rho0, tag=-1)                       # all four walls
+    assert every["wall"] == pytest.approx(6.0, rel=1e-13)
+    assert every["volume"] == w["volume"]
+
+
+def test_half_ball_on_a_wall():
+    R, d = 0.3, 0.1
+    m = inputs.box((8, 8, 4), (0, 0, 0), (1.6, 1.6, 0.8), 8, face_tags={4: 0})
+    rho0 = inputs.tanh_profile(np.sqrt(((m.node_xyz - [0.8, 0.8, 0.0]) ** 2).sum(-1)) - R, d, 1.0, 0.1)
+    w = _moments(m, "D3Q13", rho0)
+    assert w["volume"] == pytest.approx(0.5 * (4 * math.pi * R ** 3 / 3
+                                               + math.pi ** 3 * d * d * R / 12), rel=5e-6)
+    assert w["wetted"] == pytest.approx(math.pi * R * R + math.pi ** 3 * d * d / 48, rel=5e-6)
+    assert w["wall"] == pytest.approx(1.6 * 1.6, rel=1e-13)
+    assert w["wet_centroid"][:2] == pytest.approx([0.8, 0.8], abs=1e-12)
+
+
+def test_liquid_everywhere():
+    m = inputs.box((3, 2), (0, 0), (1.5, 1.0), 5, face_tags={0: 1, 2: 0})
+    w = _moments(m, "D2Q9", np.ones(m.global_id.shape))
+    assert w["volume"] == pytest.approx(1.5, rel=1e-13)
+    assert w["wetted"] == pytest.approx(w["wall"], rel=1e-13) and w["wall"] == pytest.approx(1.5)
+    assert _moments(m, "D2Q9", np.ones(m.global_id.shape), tag=1)["wall"] == pytest.approx(1.0)
+
+
+@pytest.mark.parametrize("deg", [15, 45, 90, 135, 170])
+def test_sharp_caps_invert_exactly(deg):
+    t, R = math.radians(deg), 0.37
+    area = R * R * (t - math.sin(t) * math.cos(t))
+    vol = math.pi * R ** 3 * (1 - math.cos(t)) ** 2 * (2 + math.cos(t)) / 3
+    b = R * math.sin(t)
+    assert math.degrees(wetting.cap_angle_2d(area, 2 * b)) == pytest.approx(deg, abs=1e-9)
+    assert math.degrees(wetting.cap_angle_3d(vol, math.pi * b * b)) == pytest.approx(deg, abs=1e-9)
+
+
+@pytest.mark.parametrize("deg", [30, 60, 90, 120, 150])
+def test_diffuse_caps_on_a_flat_wall(deg):
+    d = 0.1
+    m = inputs.box((16, 8), (0, 0), (2, 1), 8, face_tags={2: 0})
+    rho0 = inputs.sessile_cap_density(m, 1.0, 0.5 * math.pi * 0.3 ** 2, math.radians(deg), d)
+    w = _moments(m, "D2Q9", rho0)
+    assert wetting.contact_angle(w, 2, delta=d) == pytest.approx(deg, abs=2.0)
+
+
+@pytest.mark.parametrize("deg", [60, 90, 120])
+def test_diffuse_caps_on_a_flat_wall_3d(deg):
+    d = 0.1
+    m = inputs.box((8, 8, 4), (0, 0, 0), (1, 1, 0.5), 6, face_tags={4: 0})
+    rho0 = inputs.sessile_cap_density_3d(m, 0.5, 0.5, 2 * math.pi * 0.25 ** 3 / 3, math.radians(deg), d)
+    w = _moments(m, "D3Q13", rho0)
+    assert wetting.contact_angle(w, 3, delta=d) == pytest.approx(deg, abs=2.0)
