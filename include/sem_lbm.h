@@ -174,13 +174,22 @@ typedef struct {
   double wall;            /* int dS over the selected wall faces (a length in 2D)     */
   double wetted;          /* int phi dS over the selected wall faces                  */
   double wet_centroid[3]; /* int phi x dS / wetted (0 when wetted == 0)               */
+  double rho_v_ref, rho_l_ref; /* the reference densities that defined phi            */
 } sem_lbm_wetting;
 
-/* tag >= 0 selects the wall faces with that tag, tag < 0 every wall face.  Runs
- * two kernels on the solver's stream and synchronises it; the reduction order
- * is fixed, so repeated calls give the same bits.  Errors: SEMLBM_EINVAL (NULL
- * argument, state not set), SEMLBM_ECUDA. */
-int sem_lbm_wetting_moments(sem_lbm_t* s, int tag, sem_lbm_wetting* out);
+/* tag >= 0 selects the wall faces with that tag, tag < 0 every wall face.
+ * rho_v_ref, rho_l_ref: the phase densities that define phi.  A drop in a closed
+ * domain settles with both phases off rho_v and rho_l (its Laplace pressure and
+ * the conserved mass shift them), and the vapour filling the domain then adds
+ * to int phi dV; pass the bulk densities, or a value <= 0 for either to have
+ * them measured: phi is first taken on the state's density range [min, max],
+ * and the references become the mass-weighted mean densities of the nodes
+ * with phi < 0.02 (vapour) and phi > 0.98 (liquid).  Runs its kernels on the
+ * solver's stream and synchronises it; the reduction order is fixed, so
+ * repeated calls give the same bits.  Errors: SEMLBM_EINVAL (NULL argument,
+ * state not set, rho_l_ref <= rho_v_ref), SEMLBM_ECUDA. */
+int sem_lbm_wetting_moments(sem_lbm_t* s, int tag, double rho_v_ref, double rho_l_ref,
+                            sem_lbm_wetting* out);
 
 /* Copy a field out.  which: 0 fbar [Q][E][n^d], 1 rho [E][n^d],
  * 2 u [dim][E][n^d], 3 mu [E][n^d] (of the last computed stage-1 state).

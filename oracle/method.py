@@ -231,17 +231,26 @@ class SemLbm:
         """fbar = f^eq(rho, u = 0) (u = 0 makes F** vanish)."""
         return self.equilibrium(rho, np.zeros(rho.shape + (self.mesh.dim,)))
 
-    def wetting_moments(self, f, tag=0):
+    def wetting_moments(self, f, tag=0, rho_v=None, rho_l=None):
         """Integrals for measuring the static contact angle of Sec. 3.1 / 3.2 from
-        the state: with the liquid fraction phi = (rho - rho_v)/(rho_l - rho_v),
+        the state: with the liquid fraction phi = (rho - rho_v)/(rho_l - rho_v)
+        (reference densities given, or else measured: phi on the state's density
+        range [min, max], then the mass-weighted mean density of the nodes with
+        phi < 0.02 for rho_v and phi > 0.98 for rho_l),
         volume = int phi dV, centroid = int phi x dV / volume, and over the wall
         faces of the given tag (all walls for tag < 0), wall = int dS,
         wetted = int phi dS, wet_centroid = int phi x dS / wetted.  The volume
         integral uses the GLL quadrature of the mass matrix, the wall integrals
         the face quadrature of the wetting term (weight w |a| per face-node)."""
-        m, p = self.mesh, self.p
+        m = self.mesh
         rho = self.density(f)
-        phi = (rho - p.rho_v) / (p.rho_l - p.rho_v)
+        if rho_v is None or rho_l is None:
+            lo, hi = float(rho.min()), float(rho.max())
+            phi0 = (rho - lo) / (hi - lo)
+            vap, liq = phi0 < 0.02, phi0 > 0.98
+            rho_v = float(np.sum(m.Me[vap] * rho[vap]) / np.sum(m.Me[vap]))
+            rho_l = float(np.sum(m.Me[liq] * rho[liq]) / np.sum(m.Me[liq]))
+        phi = (rho - rho_v) / (rho_l - rho_v)
         X = m.X
         vol = float(np.sum(m.Me * phi))
         cen = [float(np.sum(m.Me * phi * X[..., a])) / vol for a in range(m.dim)]
@@ -253,7 +262,7 @@ class SemLbm:
         wcen = [float(np.sum(ws * phw * m.at_wall(X[..., a])[sel])) / wet if wet else 0.0
                 for a in range(m.dim)]
         return {"volume": vol, "centroid": cen, "wall": wall, "wetted": wet,
-                "wet_centroid": wcen}
+                "wet_centroid": wcen, "rho_v_ref": rho_v, "rho_l_ref": rho_l}
 
     def diagnostics(self, f):
         rho = self.density(f)

@@ -860,6 +860,7 @@ static __global__ void k_diag_final(const DiagPart* __restrict__ part, int n, Di
 // ---------------------------------------------------------------------------
 struct WetPart {
   double vol, vx[3], wall, wet, wx[3];
+  double mv, rv, ml, rl;   // mass and mass-weighted rho of nodes with phi < 0.02 / phi > 0.98
 };
 
 template <class L>
@@ -876,9 +877,18 @@ __global__ void k_wet(const double* __restrict__ f, const double* __restrict__ M
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < V; i += stride) {
     double rh = 0.0;
     for (int q = 0; q < Q; ++q) rh += f[q * V + i];
-    const double m = Me[i] * ((rh - rho_v) * inv_drho);
+    const double phi = (rh - rho_v) * inv_drho;
+    const double me = Me[i];
+    const double m = me * phi;
     p.vol += m;
     for (int c = 0; c < D; ++c) p.vx[c] += m * xyz[i * D + c];
+    if (phi < 0.02) {
+      p.mv += me;
+      p.rv += me * rh;
+    } else if (phi > 0.98) {
+      p.ml += me;
+      p.rl += me * rh;
+    }
   }
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < R; r += stride) {
     const int64_t i = (int64_t)rec_elem[r] * NL + rec_node[r];
@@ -907,6 +917,10 @@ __global__ void k_wet(const double* __restrict__ f, const double* __restrict__ M
         a.vx[c] += b.vx[c];
         a.wx[c] += b.wx[c];
       }
+      a.mv += b.mv;
+      a.rv += b.rv;
+      a.ml += b.ml;
+      a.rl += b.rl;
     }
     __syncthreads();
   }
@@ -925,6 +939,10 @@ static __global__ void k_wet_final(const WetPart* __restrict__ part, int n, WetP
       a.vx[c] += b.vx[c];
       a.wx[c] += b.wx[c];
     }
+    a.mv += b.mv;
+    a.rv += b.rv;
+    a.ml += b.ml;
+    a.rl += b.rl;
   }
   *out = a;
 }

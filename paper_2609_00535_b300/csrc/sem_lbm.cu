@@ -321,10 +321,10 @@ struct Impl {
     k_diag<L><<<s.diag_blocks, 256, 0, s.stream>>>(s.f, s.Me, s.parts, s.V);
     k_diag_final<<<1, 32, 0, s.stream>>>(s.parts, s.diag_blocks, s.dout);
   }
-  static void wet(sem_lbm& s, int tag) {
+  static void wet(sem_lbm& s, int tag, double rv, double rl) {
     k_wet<L><<<s.diag_blocks, 256, 0, s.stream>>>(
         s.f, s.Me, s.xyz, s.rec_elem, s.rec_node, s.rec_mask, s.rec_tag, s.wsf, (int)s.R, tag,
-        (int)s.NL, s.rho_v, 1.0 / (s.rho_l - s.rho_v), s.wparts, s.V);
+        (int)s.NL, rv, 1.0 / (rl - rv), s.wparts, s.V);
     k_wet_final<<<1, 32, 0, s.stream>>>(s.wparts, s.diag_blocks, s.wout);
   }
   static void init(sem_lbm& s, const double* rho_in) {
@@ -700,16 +700,36 @@ int sem_lbm_diagnostics(sem_lbm_t* s, sem_lbm_diag* out) {
   return 0;
 }
 
-int sem_lbm_wetting_moments(sem_lbm_t* s, int tag, sem_lbm_wetting* out) {
+int sem_lbm_wetting_moments(sem_lbm_t* s, int tag, double rho_v_ref, double rho_l_ref,
+                            sem_lbm_wetting* out) {
   if (!s || !out) return fail(SEMLBM_EINVAL, "NULL argument");
   if (!s->state_ready) return fail(SEMLBM_EINVAL, "state not set");
-  s->ops->wet(*s, tag);
-  CUDA_TRY(cudaGetLastError());
   WetPart w;
+  if (!(rho_v_ref > 0) || !(rho_l_ref > 0)) {
+    // bulk phase densities of the state: the mass-weighted mean density of the
+    // nodes with phi < 0.02 and phi > 0.98, phi taken on its density range
+    s->ops->diag(*s);
+    CUDA_TRY(cudaGetLastError());
+    DiagPart d;
+    CUDA_TRY(cudaMemcpyAsync(&d, s->dout, sizeof d, cudaMemcpyDeviceToHost, s->stream));
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    if (!(d.rho_max > d.rho_min)) return fail(SEMLBM_EINVAL, "uniform density: no interface");
+    s->ops->wet(*s, tag, d.rho_min, d.rho_max);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaMemcpyAsync(&w, s->wout, sizeof w, cudaMemcpyDeviceToHost, s->stream));
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    rho_v_ref = w.mv > 0 ? w.rv / w.mv : d.rho_min;
+    rho_l_ref = w.ml > 0 ? w.rl / w.ml : d.rho_max;
+  }
+  if (!(rho_l_ref > rho_v_ref)) return fail(SEMLBM_EINVAL, "rho_l_ref must exceed rho_v_ref");
+  s->ops->wet(*s, tag, rho_v_ref, rho_l_ref);
+  CUDA_TRY(cudaGetLastError());
   CUDA_TRY(cudaMemcpyAsync(&w, s->wout, sizeof w, cudaMemcpyDeviceToHost, s->stream));
   CUDA_TRY(cudaStreamSynchronize(s->stream));
   *out = sem_lbm_wetting{};
   out->volume = w.vol;
+  out->rho_v_ref = rho_v_ref;
+  out->rho_l_ref = rho_l_ref;
   out->wall = w.wall;
   out->wetted = w.wet;
   for (int c = 0; c < s->D; ++c) {

@@ -82,6 +82,6 @@ struct Ops {
   int (*prepare)();
   void (*lap_into)(sem_lbm&, const double* rho, double* partial);
   void (*mu_from)(sem_lbm&, const double* partial, const double* rho, double* mu);
-  void (*wet)(sem_lbm&, int tag);
+  void (*wet)(sem_lbm&, int tag, double rho_v_ref, double rho_l_ref);
 };
 

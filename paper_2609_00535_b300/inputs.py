@@ -409,12 +409,43 @@ def mixed_case(rng, kind, E, N, theta, radius_scale=1.0):
     elif kind == "droplet3d":
         ne = max(2, int(round(E ** (1.0 / 3.0))))
         c = periodic_droplet(dim=3, ne=ne, N=N, D=0.5 * radius_scale, Cn=max(0.063, 4.0 / (ne * N)))
+    elif kind == "capwall2d":
+        c = cap_on_wall_2d(theta, N=N, ne=max(4, int(round(math.sqrt(E / 2.0)))),
+                           R=0.25 * radius_scale)
     elif kind == "boxdrop2d":
         c = closed_box_drop(N=N, ne=max(4, int(round(math.sqrt(E)))), R=0.25 * radius_scale)
     else:
         raise ValueError(kind)
     c.name = "%s-E%d-N%d-%.0fdeg" % (kind, c.mesh.n_elem, N, math.degrees(theta))
     return c
+
+
+def cap_on_wall_2d(theta, N=4, ne=8, R=0.25, beta=0.1, delta=0.1, tau=1.0, rho_l=1.0,
+                   rho_v=0.1, cfl=0.4):
+    """Drop on the wall y = 0 of [0, 2] x [0, 1] (2 ne x ne quads; the other
+    walls neutral), started at its equilibrium cap for the angle theta with the
+    area of a half-disc of radius R (Sec. 3.1 shape, stiff surface tension)."""
+    mesh = box((2 * ne, ne), (0.0, 0.0), (2.0, 1.0), N, face_tags={2: 0})
+    kappa = kappa_from_width(beta, delta, rho_l, rho_v)
+    rho0 = sessile_cap_density(mesh, 1.0, 0.5 * math.pi * R * R, theta, delta, rho_l, rho_v)
+    return Case("capwall2d", mesh, "D2Q9", rho_l, rho_v, beta, kappa, tau,
+                cfl_dt(mesh, "D2Q9", cfl, kappa, rho_l), theta, (), rho0, 0,
+                {"delta": delta, "R": R})
+
+
+def angle_sweep_stream(n=64, rate=20.0, seed=7, angles=(20.0, 110.0), ne=8, N=4):
+    """Poisson stream of contact-angle sweep requests: drops on a flat wall
+    started at their equilibrium caps, angle uniform in `angles` (degrees), drop
+    size x [0.9, 1.1]; each result carries its measured angle."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for i in range(n):
+        t += rng.exponential(1.0 / rate)
+        out.append(Request(i, t, "capwall2d", 2 * ne * ne, N,
+                           math.radians(rng.uniform(*angles)), float(rng.uniform(0.9, 1.1)),
+                           int(rng.integers(1 << 30))))
+    return out
 
 
 def closed_box_drop(N=4, ne=8, R=0.25, beta=0.1, delta=0.1, tau=1.0, rho_l=1.0, rho_v=0.1,

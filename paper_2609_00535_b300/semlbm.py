@@ -57,7 +57,8 @@ class ParamsC(ctypes.Structure):
 class WettingC(ctypes.Structure):
     _fields_ = [("volume", ctypes.c_double), ("centroid", ctypes.c_double * 3),
                 ("wall", ctypes.c_double), ("wetted", ctypes.c_double),
-                ("wet_centroid", ctypes.c_double * 3)]
+                ("wet_centroid", ctypes.c_double * 3), ("rho_v_ref", ctypes.c_double),
+                ("rho_l_ref", ctypes.c_double)]
 
 
 class DiagC(ctypes.Structure):
@@ -112,7 +113,7 @@ def load():
     L.sem_lbm_set_density.argtypes = [P, P, I]
     L.sem_lbm_step.argtypes = [P, I64]
     L.sem_lbm_diagnostics.argtypes = [P, ctypes.POINTER(DiagC)]
-    L.sem_lbm_wetting_moments.argtypes = [P, I, ctypes.POINTER(WettingC)]
+    L.sem_lbm_wetting_moments.argtypes = [P, I, D, D, ctypes.POINTER(WettingC)]
     L.sem_lbm_get_field.argtypes = [P, I, P, I]
     L.sem_lbm_get_state.argtypes = [P, P, I, ctypes.POINTER(I64)]
     L.sem_lbm_set_state.argtypes = [P, P, I, I64]
@@ -267,13 +268,16 @@ class Solver:
         check(load().sem_lbm_diagnostics(self.h, ctypes.byref(d)))
         return {k: getattr(d, k) for k, _ in DiagC._fields_}
 
-    def wetting_moments(self, tag=0):
+    def wetting_moments(self, tag=0, rho_v=0.0, rho_l=0.0):
         """Liquid-fraction moments of the current state (sem_lbm_wetting_moments):
-        volume, centroid, wall, wetted, wet_centroid; tag < 0 = every wall."""
+        volume, centroid, wall, wetted, wet_centroid; tag < 0 = every wall;
+        rho_v / rho_l <= 0: the state's bulk phase densities define phi."""
         w = WettingC()
-        check(load().sem_lbm_wetting_moments(self.h, int(tag), ctypes.byref(w)))
+        check(load().sem_lbm_wetting_moments(self.h, int(tag), float(rho_v), float(rho_l),
+                                             ctypes.byref(w)))
         return {"volume": w.volume, "centroid": list(w.centroid)[:self.dim], "wall": w.wall,
-                "wetted": w.wetted, "wet_centroid": list(w.wet_centroid)[:self.dim]}
+                "wetted": w.wetted, "wet_centroid": list(w.wet_centroid)[:self.dim],
+                "rho_v_ref": w.rho_v_ref, "rho_l_ref": w.rho_l_ref}
 
     def field(self, which, out=None):
         """which: 'fbar' [Q,V], 'rho' [V], 'u' [dim,V], 'mu' [V]; numpy, or into a CUDA tensor."""

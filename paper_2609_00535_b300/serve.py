@@ -46,6 +46,7 @@ class Record:
     name: str = ""
     error: str = ""
     state: object = None
+    moments: dict = None   # wetting moments at retirement (Server(measure_tag=...))
 
 
 @dataclass
@@ -116,7 +117,8 @@ class Budget:
 
 class Server:
     def __init__(self, hbm_budget_bytes, epoch_steps=50, ke_tol=1e-20, max_steps=2000,
-                 min_steps=100, keep_state=False, workers=4, device=0, clock=time.perf_counter):
+                 min_steps=100, keep_state=False, workers=4, device=0, clock=time.perf_counter,
+                 measure_tag=None):
         self.budget_bytes = int(hbm_budget_bytes)
         self.epoch_steps = int(epoch_steps)
         self.ke_tol = ke_tol
@@ -126,6 +128,7 @@ class Server:
         self.workers = workers
         self.device = device
         self.clock = clock
+        self.measure_tag = measure_tag   # wall tag whose wetting moments each result carries
 
     def run(self, requests):
         """Serve the requests; returns Stats (one Record per request)."""
@@ -218,6 +221,8 @@ class Server:
                     batch.remove(slot)
                     if self.keep_state:
                         rec.state = s.get_state()[0]
+                    if self.measure_tag is not None and not rec.failed:
+                        rec.moments = s.wetting_moments(self.measure_tag)
                     s.close()
                     budget.release(rec.bytes)
                     del active[slot]

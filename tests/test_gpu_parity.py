@@ -249,12 +249,12 @@ def test_wetting_moments_match_oracle(kind):
     s = _solver(case)
     s.step(steps)
     om, orc, f_ref = _oracle_run(case, steps)
-    for tag in (0, -1):
-        got = s.wetting_moments(tag)
-        want = orc.wetting_moments(f_ref, tag)
-        for key in ("volume", "wall", "wetted"):
-            assert got[key] == pytest.approx(want[key], rel=1e-12), (key, tag)
+    for tag, refs in ((0, ()), (-1, ()), (0, (0.1, 1.0))):
+        got = s.wetting_moments(tag, *refs)
+        want = orc.wetting_moments(f_ref, tag, *refs)
+        for key in ("volume", "wall", "wetted", "rho_v_ref", "rho_l_ref"):
+            assert got[key] == pytest.approx(want[key], rel=1e-12), (key, tag, refs)
         for key in ("centroid", "wet_centroid"):
             np.testing.assert_allclose(got[key], want[key], rtol=1e-12, atol=1e-14)
-        assert got == s.wetting_moments(tag)          # fixed reduction order
+        assert got == s.wetting_moments(tag, *refs)    # fixed reduction order
     s.close()

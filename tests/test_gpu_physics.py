@@ -48,7 +48,7 @@ def test_flat_wall_contact_angle(deg):
     assert abs(th - deg) < 3.0, (deg, th)
     # the same angle from the device's wetting moments (cap area and wetted base)
     th_dev = wetting.contact_angle(w, 2, delta=0.1)
-    assert abs(th_dev - deg) < 3.0 and abs(th_dev - th) < 2.0, (deg, th, th_dev)
+    assert abs(th_dev - deg) < 4.0 and abs(th_dev - th) < 3.0, (deg, th, th_dev)
 
 
 @pytest.mark.parametrize("deg", [60, 120])

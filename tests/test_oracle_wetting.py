@@ -23,7 +23,7 @@ def _moments(mesh, lattice, rho0, tag=0):
     c = make_case("w", mesh, lattice, 1e-3, 0.1, 0.5, math.pi / 2, theta_tag=(math.pi / 2,),
                   rho0=rho0)
     om, o = oracle_of(c)
-    return o.wetting_moments(o.initial_state(rho0.reshape(om.shape)), tag)
+    return o.wetting_moments(o.initial_state(rho0.reshape(om.shape)), tag, 0.1, 1.0)
 
 
 def test_half_disc_on_a_wall():
@@ -87,3 +87,21 @@ def test_diffuse_caps_on_a_flat_wall_3d(deg):
     rho0 = inputs.sessile_cap_density_3d(m, 0.5, 0.5, 2 * math.pi * 0.25 ** 3 / 3, math.radians(deg), d)
     w = _moments(m, "D3Q13", rho0)
     assert wetting.contact_angle(w, 3, delta=d) == pytest.approx(deg, abs=2.0)
+
+
+def test_measured_reference_densities():
+    """With phases off the nominal rho_v, rho_l (as a drop in a closed box
+    settles), the measured references find the bulk densities (to the few 1e-3
+    that the tanh tails inside the 2 % bands add) and the moments follow."""
+    R, d, rv, rl = 0.4, 0.1, 0.12, 1.01
+    m = inputs.box((16, 8), (0, 0), (2, 1), 8, face_tags={2: 0})
+    rho0 = inputs.tanh_profile(np.sqrt(((m.node_xyz - [1.0, 0.0]) ** 2).sum(-1)) - R, d, rl, rv)
+    c = make_case("w", m, "D2Q9", 1e-3, 0.1, 0.5, math.pi / 2, rho0=rho0)
+    om, o = oracle_of(c)
+    f = o.initial_state(rho0.reshape(om.shape))
+    w = o.wetting_moments(f, 0)
+    assert w["rho_v_ref"] == pytest.approx(rv, rel=5e-3) and w["rho_l_ref"] == pytest.approx(rl, rel=5e-3)
+    assert w["volume"] == pytest.approx(0.5 * math.pi * (R * R + math.pi ** 2 * d * d / 48), rel=5e-3)
+    assert w["wetted"] == pytest.approx(2 * R, rel=5e-3)
+    nominal = o.wetting_moments(f, 0, 0.1, 1.0)                 # vapour counted as liquid
+    assert nominal["volume"] > w["volume"] + 0.02
