@@ -409,9 +409,9 @@ def mixed_case(rng, kind, E, N, theta, radius_scale=1.0):
     elif kind == "droplet3d":
         ne = max(2, int(round(E ** (1.0 / 3.0))))
         c = periodic_droplet(dim=3, ne=ne, N=N, D=0.5 * radius_scale, Cn=max(0.063, 4.0 / (ne * N)))
-    elif kind == "capwall2d":
+    elif kind in ("capwall2d", "discwall2d"):
         c = cap_on_wall_2d(theta, N=N, ne=max(4, int(round(math.sqrt(E / 2.0)))),
-                           R=0.25 * radius_scale)
+                           R=0.25 * radius_scale, init="cap" if kind == "capwall2d" else "disc")
     elif kind == "boxdrop2d":
         c = closed_box_drop(N=N, ne=max(4, int(round(math.sqrt(E)))), R=0.25 * radius_scale)
     else:
@@ -421,28 +421,32 @@ def mixed_case(rng, kind, E, N, theta, radius_scale=1.0):
 
 
 def cap_on_wall_2d(theta, N=4, ne=8, R=0.25, beta=0.1, delta=0.1, tau=1.0, rho_l=1.0,
-                   rho_v=0.1, cfl=0.4):
+                   rho_v=0.1, cfl=0.4, init="cap"):
     """Drop on the wall y = 0 of [0, 2] x [0, 1] (2 ne x ne quads; the other
-    walls neutral), started at its equilibrium cap for the angle theta with the
-    area of a half-disc of radius R (Sec. 3.1 shape, stiff surface tension)."""
+    walls neutral) with the area of a half-disc of radius R (Sec. 3.1 shape,
+    stiff surface tension), started at its equilibrium cap for the angle theta
+    (init "cap") or as the half-disc (init "disc", the 90-degree cap)."""
     mesh = box((2 * ne, ne), (0.0, 0.0), (2.0, 1.0), N, face_tags={2: 0})
     kappa = kappa_from_width(beta, delta, rho_l, rho_v)
-    rho0 = sessile_cap_density(mesh, 1.0, 0.5 * math.pi * R * R, theta, delta, rho_l, rho_v)
-    return Case("capwall2d", mesh, "D2Q9", rho_l, rho_v, beta, kappa, tau,
+    shape = theta if init == "cap" else math.pi / 2
+    rho0 = sessile_cap_density(mesh, 1.0, 0.5 * math.pi * R * R, shape, delta, rho_l, rho_v)
+    return Case("capwall2d" if init == "cap" else "discwall2d", mesh, "D2Q9", rho_l, rho_v, beta,
+                kappa, tau,
                 cfl_dt(mesh, "D2Q9", cfl, kappa, rho_l), theta, (), rho0, 0,
                 {"delta": delta, "R": R})
 
 
-def angle_sweep_stream(n=64, rate=20.0, seed=7, angles=(20.0, 110.0), ne=8, N=4):
+def angle_sweep_stream(n=64, rate=20.0, seed=7, angles=(20.0, 110.0), ne=8, N=4, init="cap"):
     """Poisson stream of contact-angle sweep requests: drops on a flat wall
-    started at their equilibrium caps, angle uniform in `angles` (degrees), drop
-    size x [0.9, 1.1]; each result carries its measured angle."""
+    started at their equilibrium caps (init "cap") or as half-discs ("disc"),
+    angle uniform in `angles` (degrees), drop size x [0.9, 1.1]; the same seed
+    gives the same angles and sizes for both starts."""
     rng = np.random.default_rng(seed)
     t = 0.0
     out = []
     for i in range(n):
         t += rng.exponential(1.0 / rate)
-        out.append(Request(i, t, "capwall2d", 2 * ne * ne, N,
+        out.append(Request(i, t, "capwall2d" if init == "cap" else "discwall2d", 2 * ne * ne, N,
                            math.radians(rng.uniform(*angles)), float(rng.uniform(0.9, 1.1)),
                            int(rng.integers(1 << 30))))
     return out

@@ -61,6 +61,8 @@ def cap_angle_3d(volume, wetted, delta=0.0, iters=20):
     for _ in range(iters if delta > 0 else 0):
         s = math.sin(theta)
         aw = wetted - math.pi ** 3 * (delta / s) ** 2 / 48
+        if aw <= 0:      # contact circle no wider than the interface: no correction
+            return _bisect(_g3, volume / wetted ** 1.5)
         R = math.sqrt(aw / math.pi) / s
         v = volume - math.pi ** 3 * delta ** 2 * R * (1 - math.cos(theta)) / 24
         theta = _bisect(_g3, v / aw ** 1.5)
