@@ -94,6 +94,11 @@ def cap_angle_from_centroid(volume, height, dim):
     return _bisect(_h2 if dim == 2 else _h3, height / volume ** (1.0 / dim))
 
 
+def _check(volume, base):
+    if not (volume > 0 and base > 0):
+        raise ValueError("no drop on the wall (volume %g, wetted %g)" % (volume, base))
+
+
 def contact_angle(moments, dim, delta=0.0, method="base"):
     """Degrees, for a drop on a flat wall; moments as returned by
     Solver.wetting_moments.  method "base": liquid volume and wetted base;
@@ -103,5 +108,6 @@ def contact_angle(moments, dim, delta=0.0, method="base"):
         ax = dim - 1
         height = abs(moments["centroid"][ax] - moments["wet_centroid"][ax])
         return math.degrees(cap_angle_from_centroid(moments["volume"], height, dim))
+    _check(moments["volume"], moments["wetted"])
     f = cap_angle_2d if dim == 2 else cap_angle_3d
     return math.degrees(f(moments["volume"], moments["wetted"], delta))
