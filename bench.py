@@ -288,6 +288,51 @@ def converging_serving_section(args, device):
     return out
 
 
+def angle_sweep_section(args, device):
+    """Contact-angle sweep through the server: drops on a flat wall run until
+    KE_max < 1e-20, each started at its equilibrium cap and, as a comparison
+    stream with the same angles and sizes, as a half-disc; every converged
+    result's angle is measured from the device's wetting moments."""
+    import math
+    from paper_2609_00535_b300 import serve, wetting
+    out = {"workload": "flat-wall drops 2D, 16x8 quads, N 4, beta 0.1, delta 0.1, "
+                       "angles 20-100 deg, R 0.225-0.275",
+           "requests": args.sweep_requests, "ke_tol": 1e-20, "max_steps": args.sweep_max_steps}
+    steps_by = {}
+    for init in ("cap", "disc"):
+        reqs = inputs.angle_sweep_stream(n=args.sweep_requests, rate=50.0, seed=7,
+                                         angles=(20.0, 100.0), init=init)
+        srv = serve.Server(hbm_budget_bytes=int(args.serve_budget_gb * 2 ** 30), epoch_steps=1000,
+                           ke_tol=1e-20, max_steps=args.sweep_max_steps, min_steps=1000,
+                           measure_tag=0)
+        st = srv.run(reqs)
+        summ = st.summary()
+        by = {r.rid: r for r in st.records}
+        errs = []
+        steps_by[init] = {}
+        for q in reqs:
+            r = by[q.rid]
+            if r.converged and r.moments:
+                steps_by[init][q.rid] = r.steps
+                try:
+                    errs.append(wetting.contact_angle(r.moments, 2, delta=0.1) - math.degrees(q.theta))
+                except ValueError:
+                    pass
+        steps = sorted(steps_by[init].values())
+        errs.sort(key=abs)
+        out[init] = {"converged": summ["converged"], "capped": summ["capped"],
+                     "failed": summ["failed"], "p50_s": summ["p50_s"], "p99_s": summ["p99_s"],
+                     "node_updates_per_s": summ["node_updates_per_s"],
+                     "median_steps_to_converge": steps[len(steps) // 2] if steps else None,
+                     "angle_err_deg_median": errs[len(errs) // 2] if errs else None,
+                     "angle_err_deg_max_abs": abs(errs[-1]) if errs else None}
+    both = [q for q in steps_by["cap"] if q in steps_by["disc"]]
+    if both:
+        out["steps_cap_over_disc"] = (sum(steps_by["cap"][q] for q in both)
+                                      / sum(steps_by["disc"][q] for q in both))
+    return out
+
+
 def native_arm(args):
     import numpy as np
     import torch
@@ -384,11 +429,12 @@ def native_arm(args):
         batched = serving = None
         if not args.no_batched:
             batched = batched_section(args, device)
-        serving_converge = None
+        serving_converge = sweep = None
         if not args.no_serving:
             cap = batched["batched_node_updates_per_s"] if batched else value
             serving = serving_section(args, device, cap)
             serving_converge = converging_serving_section(args, device)
+            sweep = angle_sweep_section(args, device)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -426,6 +472,7 @@ def native_arm(args):
             "batched": batched,
             "serving": serving,
             "serving_to_convergence": serving_converge,
+            "angle_sweep": sweep,
             "final_diag": {"ke_max": d["ke_max"], "mass": d["mass"], "status": d["status"]},
         }
         print(json.dumps(line), flush=True)
@@ -454,6 +501,8 @@ def main():
     ap.add_argument("--serve-budget-gb", type=float, default=40.0)
     ap.add_argument("--converge-requests", type=int, default=100)
     ap.add_argument("--converge-rate", type=float, default=20.0)
+    ap.add_argument("--sweep-requests", type=int, default=32)
+    ap.add_argument("--sweep-max-steps", type=int, default=100000)
     ap.add_argument("--ne", type=int, default=None,
                     help="elements per axis of the sphere-cap mesh (profiling cases only)")
     args = ap.parse_args()

@@ -258,3 +258,15 @@ def test_wetting_moments_match_oracle(kind):
             np.testing.assert_allclose(got[key], want[key], rtol=1e-12, atol=1e-14)
         assert got == s.wetting_moments(tag, *refs)    # fixed reduction order
     s.close()
+
+
+@pytest.mark.parametrize("rho_v,cfl,steps", [(0.01, 0.4, 300), (0.001, 0.05, 200)])
+def test_high_density_ratio(rho_v, cfl, steps):
+    """Density ratios 100 and 1000 (the paper notes larger ratios are possible,
+    Appendix A): a 60-degree cap on a flat wall.  Ratio 1000 needs the smaller
+    time step (at CFL 0.4 the oracle itself turns non-finite within 250 steps)."""
+    m = inputs.box((8, 8), (0, 0), (1, 1), 4, face_tags={2: 0})
+    c = make_case("ratio", m, "D2Q9", 0.1, 0.1, 1.0, math.radians(60), rho_v=rho_v, cfl=cfl,
+                  rho0=inputs.sessile_cap_density(m, 0.5, 0.5 * math.pi * 0.25 ** 2,
+                                                  math.radians(60), 0.1, 1.0, rho_v))
+    _compare(c, steps)
