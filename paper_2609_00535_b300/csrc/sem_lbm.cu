@@ -306,7 +306,12 @@ struct Impl {
     k_dss_collide<L><<<grid_of(s.G, kDssThreads), kDssThreads, 0, s.stream>>>(s.view);
   }
   static void rhs(sem_lbm& s, const double* gst) {
-    k_rhs<L, NP, EPB><<<blocks(s), THREADS, SM_RHS, s.stream>>>(s.view, gst);
+    // small meshes: split the velocity pairs over up to NREP CTAs per element
+    // batch until the grid reaches two CTAs per SM
+    const int nb = blocks(s);
+    int P = 1;
+    while (P < L::NREP && (int64_t)nb * P < 2 * (int64_t)s.n_sm) ++P;
+    k_rhs<L, NP, EPB><<<dim3(nb, P), THREADS, SM_RHS, s.stream>>>(s.view, gst);
   }
   static void rk(sem_lbm& s, int stage, const double* gcur, double* out) {
     const int gr = grid_of(s.G, kDssThreads);
@@ -567,6 +572,8 @@ int sem_lbm_create(const sem_lbm_mesh* mesh, int N, sem_lbm_lattice lattice, dou
   if (s->ops->prepare() != 0) return bail(fail(SEMLBM_ECUDA, "cudaFuncSetAttribute failed"));
 
   if (cudaGetDevice(&s->device) != cudaSuccess) return bail(fail(SEMLBM_ECUDA, "cudaGetDevice failed"));
+  if (cudaDeviceGetAttribute(&s->n_sm, cudaDevAttrMultiProcessorCount, s->device) != cudaSuccess)
+    return bail(fail(SEMLBM_ECUDA, "cudaDeviceGetAttribute failed"));
   if (p.stream) {
     s->stream = (cudaStream_t)p.stream;
   } else {

@@ -52,6 +52,7 @@ struct sem_lbm {
   bool moving = false;   // some wall has a non-zero velocity
   semlbm::DiagPart *parts, *dout;
   int diag_blocks = 0;
+  int n_sm = 148;                       // SMs of the device (grid sizing)
   bool state_ready = false;
   int64_t step = 0;
   semlbm::View view{};                   // device pointers + parameters, for the kernels
