@@ -507,10 +507,10 @@ __device__ __forceinline__ void body_dss_collide(const View& v, int g) {
 // a5: element-local right-hand side of the force-split streaming (Sec. 3.3)
 //   r_a = M_e [ -e_a . grad(g_a - t_a rho) - (t_a/c_s^2) rho e_a . grad(mu) ]
 //         + flux bounce-back on incoming wall directions (Sec. 2.2)
-// for the opposite-velocity pairs [pr0, pr1) of the velocity set (all by
-// default); a pair's two values do not depend on which other pairs a CTA
-// computes, so splitting the pairs over CTAs gives the same bits
-template <class L, int NP, int EPB>
+// for the opposite-velocity pairs [pr0, pr1) of the velocity set when SPLIT
+// (all pairs otherwise); a pair's two values do not depend on which other
+// pairs a CTA computes, so splitting the pairs over CTAs gives the same bits
+template <class L, int NP, int EPB, bool SPLIT = false>
 __device__ __forceinline__ void body_rhs(const View& v, const double* __restrict__ gst, int eb,
                                          double* sm, int pr0 = 0, int pr1 = L::NREP) {
   constexpr int D = L::D, Q = L::Q, NL = ipow(NP, D), NT = EPB * NL;
@@ -532,7 +532,7 @@ __device__ __forceinline__ void body_rhs(const View& v, const double* __restrict
   for (int i = threadIdx.x; i < NP * NP; i += blockDim.x) sD[i] = __ldg(Dmat + i);
   stage_in(sr, v.rho, base, count);
   stage_in(smu, v.mu, base, count);
-  if (pr0 == 0 && pr1 == L::NREP) {
+  if constexpr (!SPLIT) {
 #pragma unroll 1
     for (int q = 1; q < Q; ++q) stage_in(sg + (q - 1) * NT, gst + q * V, base, count);
   } else {
@@ -569,8 +569,10 @@ __device__ __forceinline__ void body_rhs(const View& v, const double* __restrict
   static_for<0, L::NREP>([&](auto RR) {
     constexpr int A = L::rep(decltype(RR)::value), B = L::opp(A);
     constexpr double T = L::t(A);
-    constexpr int RI = decltype(RR)::value;
-    if (RI < pr0 || RI >= pr1) return;
+    if constexpr (SPLIT) {
+      constexpr int RI = decltype(RR)::value;
+      if (RI < pr0 || RI >= pr1) return;
+    }
     double c[D];   // (M_e S J^-1 C_A)_b: M_e e_A . grad = sum_b c_b d_b
 #pragma unroll
     for (int b = 0; b < D; ++b) c[b] = L::template cdot<A>(J[b]);
@@ -697,14 +699,18 @@ __global__ void k_dss_collide(View v) {
   body_dss_collide<L>(v, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
-template <class L, int NP, int EPB>
+template <class L, int NP, int EPB, bool SPLIT>
 __global__ void __launch_bounds__(cta_threads<L::D, NP, EPB>(), rhs_min_blocks<L::D, NP, EPB>())
     k_rhs(View v, const double* __restrict__ gst) {
-  // gridDim.y > 1 splits the velocity pairs of each element batch over CTAs
-  // (meshes too small to fill the GPU with one CTA per element batch)
+  // SPLIT: the velocity pairs of each element batch are spread over gridDim.y
+  // CTAs (meshes too small to fill the GPU with one CTA per element batch)
   extern __shared__ double sm[];
-  const int P = gridDim.y, y = blockIdx.y;
-  body_rhs<L, NP, EPB>(v, gst, blockIdx.x, sm, y * L::NREP / P, (y + 1) * L::NREP / P);
+  if constexpr (SPLIT) {
+    const int P = gridDim.y, y = blockIdx.y;
+    body_rhs<L, NP, EPB, true>(v, gst, blockIdx.x, sm, y * L::NREP / P, (y + 1) * L::NREP / P);
+  } else {
+    body_rhs<L, NP, EPB>(v, gst, blockIdx.x, sm);
+  }
 }
 
 template <class L, int STAGE>

@@ -270,8 +270,10 @@ struct Impl {
   static int prepare() {
     // opt in to large dynamic shared memory where a tile needs it
     if (SM_RHS > 48 * 1024)
-      if (cudaFuncSetAttribute(k_rhs<L, NP, EPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)SM_RHS) != cudaSuccess)
+      if (cudaFuncSetAttribute(k_rhs<L, NP, EPB, false>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM_RHS) != cudaSuccess ||
+          cudaFuncSetAttribute(k_rhs<L, NP, EPB, true>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM_RHS) != cudaSuccess)
         return -1;
     if (SM_LAP > 48 * 1024)
       if (cudaFuncSetAttribute(k_lap<L, NP, EPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -311,7 +313,10 @@ struct Impl {
     const int nb = blocks(s);
     int P = 1;
     while (P < L::NREP && (int64_t)nb * P < 2 * (int64_t)s.n_sm) ++P;
-    k_rhs<L, NP, EPB><<<dim3(nb, P), THREADS, SM_RHS, s.stream>>>(s.view, gst);
+    if (P == 1)
+      k_rhs<L, NP, EPB, false><<<nb, THREADS, SM_RHS, s.stream>>>(s.view, gst);
+    else
+      k_rhs<L, NP, EPB, true><<<dim3(nb, P), THREADS, SM_RHS, s.stream>>>(s.view, gst);
   }
   static void rk(sem_lbm& s, int stage, const double* gcur, double* out) {
     const int gr = grid_of(s.G, kDssThreads);
