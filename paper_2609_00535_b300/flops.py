@@ -113,9 +113,10 @@ def step_work(lattice, N, n_local, n_groups, n_wall_nodes):
     # k_dss_mu (x3): sum of copies, 1/M, mu0 and -kappa lap
     add(10, 11, 3 * G)
     add(1, 1, 3 * X)
-    # k_force (x1): grad mu, reference (c^2 d rho - rho d mu)/S, metric M_e S J^-1
-    add(d * dv["ops"] + 1 + 2 * d + d * d,
-        d * dv["flops"] + 1 + 3 * d + d * (2 * d - 1), V)
+    # k_force (x1): grad mu, reference (c^2 d rho - rho d mu)/S (the first term
+    # scaled by the force_split factor: 1 mul), metric M_e S J^-1
+    add(d * dv["ops"] + 2 + 2 * d + d * d,
+        d * dv["flops"] + 2 + 3 * d + d * (2 * d - 1), V)
     # k_dss_collide (x1): force average, momentum, equilibrium and F**
     cd = _cdot_ops(lattice)
     mom = sum(1 + k for k in _REP_NONZERO[lattice])            # difference + components
