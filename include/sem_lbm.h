@@ -281,10 +281,12 @@ int sem_lbm_batch_add(sem_lbm_batch_t* b, sem_lbm_t* s, int* slot);
 int sem_lbm_batch_remove(sem_lbm_batch_t* b, int slot);
 /* Advances every member n_steps full steps (asynchronous). */
 int sem_lbm_batch_step(sem_lbm_batch_t* b, int64_t n_steps);
-/* Autotuner: for each group, times steps_per_candidate (>= 2) real steps of
- * every compiled tile shape and keeps the fastest (and remembers it for later
- * groups of the same velocity set, N and size in this process).  All shapes
- * give identical results; the tuning steps advance the members like any step. */
+/* Autotuner: for each group and every compiled tile shape, runs one warm-up
+ * step (drained before timing) and two timed runs of steps_per_candidate - 1
+ * (>= 1) real steps, and keeps the shape with the fastest run (remembered for
+ * later groups of the same velocity set, N and size in this process).  All
+ * shapes give identical results; the tuning steps (2 steps_per_candidate - 1
+ * per shape) advance the members like any step. */
 int sem_lbm_batch_tune(sem_lbm_batch_t* b, int steps_per_candidate);
 /* Diagnostics of slots 0..n-1 (one synchronisation); empty slots get
  * step = -1 and status = SEMLBM_EINVAL. */

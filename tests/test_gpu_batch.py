@@ -95,7 +95,7 @@ def test_autotune_keeps_results_and_picks_a_candidate():
     solvers = [_solver(c) for c in cases]
     for s in solvers:
         b.add(s)
-    b.tune(3)                            # every candidate: 3 real steps
+    b.tune(3)                            # every candidate: 1 + 2 x 2 real steps
     info = b.info()
     total = {}
     for g in info:
