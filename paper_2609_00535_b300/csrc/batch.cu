@@ -38,14 +38,12 @@ struct GroupDev {
   const WorkItem* elem;
   const WorkItem* node;
   const int* counts;   // [0] element items, [1] node items
-  int rhs_split;       // velocity-pair groups per element item in kb_rhs (1 = unsplit)
 };
 
 struct GroupOps {
   int epb = 0, threads = 0;
   size_t sm_lap = 0, sm_force = 0, sm_rhs = 0;
   int grid_lap = 0, grid_force = 0, grid_rhs = 0, grid_node = 0;
-  int nrep = 1;   // velocity pairs of the set (the most kb_rhs can split an item into)
   void (*step)(const GroupOps&, const GroupDev&, cudaStream_t) = nullptr;
 };
 
@@ -58,22 +56,15 @@ void group_step(const GroupOps& o, const GroupDev& d, cudaStream_t st) {
   kb_dss_mu<L><<<o.grid_node, kDssThreads, 0, st>>>(d.views, d.node, cn);
   kb_force<L, NP, EPB><<<o.grid_force, T, o.sm_force, st>>>(d.views, d.elem, ce);
   kb_dss_collide<L><<<o.grid_node, kDssThreads, 0, st>>>(d.views, d.node, cn);
-  auto rhs = [&](int from_fs) {
-    if (d.rhs_split > 1)
-      kb_rhs<L, NP, EPB, true><<<o.grid_rhs, T, o.sm_rhs, st>>>(d.views, d.elem, ce, from_fs,
-                                                                d.rhs_split);
-    else
-      kb_rhs<L, NP, EPB, false><<<o.grid_rhs, T, o.sm_rhs, st>>>(d.views, d.elem, ce, from_fs, 1);
-  };
-  rhs(1);
+  kb_rhs<L, NP, EPB><<<o.grid_rhs, T, o.sm_rhs, st>>>(d.views, d.elem, ce, 1);
   kb_dss_rk<L, 1><<<o.grid_node, kDssThreads, 0, st>>>(d.views, d.node, cn);
   kb_lap<L, NP, EPB><<<o.grid_lap, T, o.sm_lap, st>>>(d.views, d.elem, ce);
   kb_dss_mu<L><<<o.grid_node, kDssThreads, 0, st>>>(d.views, d.node, cn);
-  rhs(0);
+  kb_rhs<L, NP, EPB><<<o.grid_rhs, T, o.sm_rhs, st>>>(d.views, d.elem, ce, 0);
   kb_dss_rk<L, 2><<<o.grid_node, kDssThreads, 0, st>>>(d.views, d.node, cn);
   kb_lap<L, NP, EPB><<<o.grid_lap, T, o.sm_lap, st>>>(d.views, d.elem, ce);
   kb_dss_mu<L><<<o.grid_node, kDssThreads, 0, st>>>(d.views, d.node, cn);
-  rhs(0);
+  kb_rhs<L, NP, EPB><<<o.grid_rhs, T, o.sm_rhs, st>>>(d.views, d.elem, ce, 0);
   kb_dss_rk<L, 3><<<o.grid_node, kDssThreads, 0, st>>>(d.views, d.node, cn);
 }
 
@@ -103,9 +94,7 @@ void add_candidate(std::vector<GroupOps>& out, int sms) {
   if (o.sm_rhs > 227 * 1024) return;
   o.grid_lap = resident_grid(kb_lap<L, NP, EPB>, o.threads, o.sm_lap, sms);
   o.grid_force = resident_grid(kb_force<L, NP, EPB>, o.threads, o.sm_force, sms);
-  o.grid_rhs = std::min(resident_grid(kb_rhs<L, NP, EPB, false>, o.threads, o.sm_rhs, sms),
-                        resident_grid(kb_rhs<L, NP, EPB, true>, o.threads, o.sm_rhs, sms));
-  o.nrep = L::NREP;
+  o.grid_rhs = resident_grid(kb_rhs<L, NP, EPB>, o.threads, o.sm_rhs, sms);
   const int g1 = resident_grid(kb_dss_rk<L, 1>, kDssThreads, 0, sms);
   const int g2 = resident_grid(kb_dss_collide<L>, kDssThreads, 0, sms);
   o.grid_node = std::min(g1, g2);
@@ -262,16 +251,7 @@ int refresh_group(sem_lbm_batch* b, BatchGroup* g) {
   return 0;
 }
 
-// pair groups per element item: enough passes to occupy kb_rhs's resident grid
-// once (any value gives the same bits; a stale one in a captured graph only
-// costs speed)
-GroupDev dev_of(const BatchGroup* g) {
-  const GroupOps& o = g->cands[g->choice];
-  const int64_t items = g->h_counts[0];
-  int P = 1;
-  while (items > 0 && P < o.nrep && items * P < o.grid_rhs) ++P;
-  return GroupDev{g->d_views, g->d_elem, g->d_node, g->d_counts, P};
-}
+GroupDev dev_of(const BatchGroup* g) { return GroupDev{g->d_views, g->d_elem, g->d_node, g->d_counts}; }
 
 int capture(sem_lbm_batch* b) {
   if (b->graph) {

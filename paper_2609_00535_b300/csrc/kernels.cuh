@@ -776,26 +776,16 @@ __global__ void kb_dss_collide(const View* __restrict__ slots, const WorkItem* _
   }
 }
 
-// SPLIT: each work item is taken by P CTA passes, one per group of velocity
-// pairs (lists too short to occupy the resident grid)
-template <class L, int NP, int EPB, bool SPLIT>
+template <class L, int NP, int EPB>
 __global__ void __launch_bounds__(cta_threads<L::D, NP, EPB>(), rhs_min_blocks<L::D, NP, EPB>())
     kb_rhs(const View* __restrict__ slots, const WorkItem* __restrict__ items,
-           const int* __restrict__ count, int from_fs, int P) {
+           const int* __restrict__ count, int from_fs) {
   extern __shared__ double sm[];
-  const int n = *count * (SPLIT ? P : 1);
+  const int n = *count;
   for (int w = blockIdx.x; w < n; w += gridDim.x) {
-    if constexpr (SPLIT) {
-      const WorkItem it = items[w / P];
-      const int pg = w - (w / P) * P;
-      const View& v = slots[it.slot];
-      body_rhs<L, NP, EPB, true>(v, from_fs ? v.fs : v.g, it.unit, sm, pg * L::NREP / P,
-                                 (pg + 1) * L::NREP / P);
-    } else {
-      const WorkItem it = items[w];
-      const View& v = slots[it.slot];
-      body_rhs<L, NP, EPB>(v, from_fs ? v.fs : v.g, it.unit, sm);
-    }
+    const WorkItem it = items[w];
+    const View& v = slots[it.slot];
+    body_rhs<L, NP, EPB>(v, from_fs ? v.fs : v.g, it.unit, sm);
     __syncthreads();
   }
 }
