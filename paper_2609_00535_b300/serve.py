@@ -15,7 +15,8 @@ sem_lbm_batch_*) stepping on the GPU, and three kinds of work overlap:
   solver to the batch as a new slot (the running CUDA graph is not
   re-captured), reads all slots' diagnostics with one synchronisation, and
   retires the slots that converged (KE_max < ke_tol after min_steps), failed
-  (non-finite state) or used max_steps, returning their memory to the budget.
+  (non-finite state), were cancelled (Server.cancel) or used max_steps,
+  returning their memory to the budget.
 
 Every solve computes the same bits as it would alone (the batch kernels are
 the single-solve kernels over a slot table), so admission order and the mix
@@ -41,6 +42,7 @@ class Record:
     ke_max: float = None
     converged: bool = False
     failed: bool = False
+    cancelled: bool = False
     nodes: int = 0
     bytes: int = 0
     name: str = ""
@@ -74,8 +76,9 @@ class Stats:
         return {
             "requests": len(self.records), "completed": len(done),
             "converged": sum(r.converged for r in done),
-            "capped": sum((not r.converged and not r.failed) for r in done),
+            "capped": sum((not r.converged and not r.failed and not r.cancelled) for r in done),
             "failed": sum(r.failed for r in done),
+            "cancelled": sum(r.cancelled for r in done),
             "p50_s": self.percentile(50), "p99_s": self.percentile(99),
             "node_updates_per_s": self.node_updates / self.wall_s if self.wall_s else None,
             "wall_s": self.wall_s, "epochs": self.epochs, "max_slots": self.max_slots,
@@ -129,6 +132,18 @@ class Server:
         self.device = device
         self.clock = clock
         self.measure_tag = measure_tag   # wall tag whose wetting moments each result carries
+        self._cancel = set()
+        self._cancel_lock = threading.Lock()
+
+    def cancel(self, rid):
+        """Withdraw a request (from any thread): one not yet built is never built,
+        a running one is retired at the next epoch boundary; others are unaffected."""
+        with self._cancel_lock:
+            self._cancel.add(rid)
+
+    def _cancelled(self, rid):
+        with self._cancel_lock:
+            return rid in self._cancel
 
     def run(self, requests):
         """Serve the requests; returns Stats (one Record per request)."""
@@ -145,6 +160,11 @@ class Server:
         def prepare(req):
             torch.cuda.set_device(self.device)
             rec = records[req.rid]
+            if self._cancelled(req.rid):
+                rec.cancelled = True
+                rec.finished = self.clock() - t0
+                ready.put((req.rid, None))
+                return
             try:
                 case = req.case()
                 need = semlbm.workspace_bytes(case.mesh, case.mesh.N, case.lattice)
@@ -192,6 +212,13 @@ class Server:
                     if s is None:
                         finished += 1
                         continue
+                    if self._cancelled(rid):          # withdrawn while it was being built
+                        rec.cancelled = True
+                        rec.finished = self.clock() - t0
+                        s.close()
+                        budget.release(rec.bytes)
+                        finished += 1
+                        continue
                     if active:
                         stats.overlapped_admissions += 1
                     slot = batch.add(s)
@@ -213,6 +240,8 @@ class Server:
                     if d["status"] != 0:
                         rec.failed = True
                         rec.error = "status %d at step %d" % (d["status"], d["step"])
+                    elif self._cancelled(rec.rid):
+                        rec.cancelled = True
                     elif d["step"] >= self.min_steps and d["ke_max"] < self.ke_tol:
                         rec.converged = True
                     elif d["step"] < self.max_steps:
@@ -221,7 +250,7 @@ class Server:
                     batch.remove(slot)
                     if self.keep_state:
                         rec.state = s.get_state()[0]
-                    if self.measure_tag is not None and not rec.failed:
+                    if self.measure_tag is not None and not (rec.failed or rec.cancelled):
                         rec.moments = s.wetting_moments(self.measure_tag)
                     s.close()
                     budget.release(rec.bytes)

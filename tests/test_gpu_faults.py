@@ -84,3 +84,32 @@ def test_server_fails_only_the_broken_requests():
     assert by[1].failed and "status %d" % ENONFINITE in by[1].error
     assert by[2].failed and by[2].steps == 0 and by[2].error
     assert not by[0].failed and not by[3].failed and by[0].steps >= 30 and by[3].steps >= 30
+
+
+def test_cancelled_requests_leave_the_others_unchanged():
+    """One request withdrawn before it arrives (never built), one withdrawn while
+    it runs (retired at the next epoch); the rest run as they would alone."""
+    import threading
+    from paper_2609_00535_b300 import semlbm
+    reqs = [inputs.Request(i, 0.3 if i == 1 else 0.0, "flat2d", 64, 4, math.radians(40 + 10 * i),
+                           1.0, 10 + i) for i in range(4)]
+    srv = Server(hbm_budget_bytes=1 << 30, epoch_steps=500, ke_tol=0.0, max_steps=40000,
+                 min_steps=500, keep_state=True)
+    srv.cancel(1)
+    timer = threading.Timer(0.5, srv.cancel, args=(2,))
+    timer.start()
+    st = srv.run(reqs)
+    timer.join()
+    by = {r.rid: r for r in st.records}
+    assert st.summary()["cancelled"] == 2 and st.summary()["failed"] == 0
+    assert by[1].cancelled and by[1].steps == 0
+    assert by[2].cancelled and 0 < by[2].steps < 40000
+    for rid in (0, 3):
+        r = by[rid]
+        assert not r.cancelled and r.steps >= 40000
+        case = reqs[rid].case()
+        s = semlbm.Solver.from_case(case)
+        s.set_density(case.rho0)
+        s.step(r.steps)
+        assert np.array_equal(s.get_state()[0], r.state)
+        s.close()
