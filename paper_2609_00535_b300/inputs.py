@@ -546,6 +546,18 @@ def sessile_cap_density_3d(mesh, x_c, y_c, volume, theta, delta, rho_l=1.0, rho_
     return tanh_profile(dist, delta, rho_l, rho_v)
 
 
+def curved_cap_density(mesh, wall_center, Rw, Rd, theta, delta, direction, rho_l=1.0,
+                       rho_v=0.1):
+    """Drop of radius Rd on a circular (2D) or spherical (3D) wall of radius Rw
+    centred at wall_center, at its equilibrium position along the unit vector
+    `direction`: centre distance d with d^2 = Rw^2 + Rd^2 - 2 Rw Rd cos(theta)."""
+    d = math.sqrt(Rw * Rw + Rd * Rd - 2 * Rw * Rd * math.cos(theta))
+    n = np.asarray(direction, dtype=np.float64)
+    c = np.asarray(wall_center, dtype=np.float64) + d * n / np.linalg.norm(n)
+    dist = np.sqrt(((mesh.node_xyz - c) ** 2).sum(-1)) - Rd
+    return tanh_profile(dist, delta, rho_l, rho_v)
+
+
 def cylinder_cap_density(mesh, center, Rc, Rd, theta, delta, rho_l=1.0, rho_v=0.1):
     """Drop of radius Rd on a cylinder of radius Rc at its equilibrium position:
     centre distance d with d^2 = Rc^2 + Rd^2 - 2 Rc Rd cos(theta), along +y."""

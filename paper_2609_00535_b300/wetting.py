@@ -94,16 +94,93 @@ def cap_angle_from_centroid(volume, height, dim):
     return _bisect(_h2 if dim == 2 else _h3, height / volume ** (1.0 / dim))
 
 
+# ---------------------------------------------------------------------------
+# Curved walls: a drop of radius Rd on a cylinder (2D) or sphere (3D) of radius
+# Rw, centres a distance d apart with d^2 = Rw^2 + Rd^2 - 2 Rw Rd cos(theta)
+# (the equilibrium position used by inputs.cylinder_cap_density).  The liquid
+# volume is the drop's disc/ball minus the lens it shares with the wall body;
+# the wetted measure is the wall's arc/cap inside the drop.
+# ---------------------------------------------------------------------------
+def _half_angles(Rw, Rd, d):
+    ca = max(-1.0, min(1.0, (Rw * Rw + d * d - Rd * Rd) / (2 * Rw * d)))
+    cb = max(-1.0, min(1.0, (Rd * Rd + d * d - Rw * Rw) / (2 * Rd * d)))
+    return math.acos(ca), math.acos(cb)
+
+
+def curved_cap(Rw, Rd, theta, dim):
+    """(liquid volume, wetted measure) of a sharp drop of radius Rd meeting a
+    wall of radius Rw at the angle theta."""
+    d = math.sqrt(Rw * Rw + Rd * Rd - 2 * Rw * Rd * math.cos(theta))
+    a, b = _half_angles(Rw, Rd, d)
+    if dim == 2:
+        lens = Rw * Rw * a + Rd * Rd * b - d * Rw * math.sin(a)
+        return math.pi * Rd * Rd - lens, 2 * Rw * a
+    hw, hd = Rw * (1 - math.cos(a)), Rd * (1 - math.cos(b))
+    lens = math.pi * hw * hw * (3 * Rw - hw) / 3 + math.pi * hd * hd * (3 * Rd - hd) / 3
+    return 4 * math.pi * Rd ** 3 / 3 - lens, 2 * math.pi * Rw * hw
+
+
+def _excess(Rw, Rd, theta, dim, delta):
+    """Diffuse-interface excess of the volume and of the wetted measure (the
+    Sommerfeld term over the drop's free surface; the contact line as on a flat
+    wall)."""
+    if delta <= 0:
+        return 0.0, 0.0
+    d = math.sqrt(Rw * Rw + Rd * Rd - 2 * Rw * Rd * math.cos(theta))
+    _, b = _half_angles(Rw, Rd, d)
+    if dim == 2:
+        return math.pi ** 2 * delta ** 2 * 2 * (math.pi - b) / 96, 0.0
+    hd = Rd * (1 - math.cos(b))
+    dv = math.pi ** 2 * delta ** 2 * (8 * math.pi * Rd - 4 * math.pi * hd) / 96
+    return dv, math.pi ** 3 * (delta / math.sin(theta)) ** 2 / 48
+
+
+def cap_angle_on_curved_wall(volume, wetted, Rw, dim, delta=0.0, iters=20):
+    """Contact angle (radians) of a drop on a circular cylinder (2D) or a sphere
+    (3D) of radius Rw from its liquid volume and wetted measure: for each trial
+    angle the drop radius that holds the volume is found by bisection, and the
+    angle is bisected on the wetted measure (which falls as theta grows)."""
+    def size_for(theta, vol):
+        lo, hi = 1e-9, 1e3 * (Rw + vol)
+        for _ in range(200):
+            mid = 0.5 * (lo + hi)
+            if curved_cap(Rw, mid, theta, dim)[0] < vol:
+                lo = mid
+            else:
+                hi = mid
+        return 0.5 * (lo + hi)
+
+    vol, wet = volume, wetted
+    theta = math.pi / 2
+    for _ in range(iters if delta > 0 else 1):
+        lo, hi = 1e-6, math.pi - 1e-6
+        for _ in range(100):
+            mid = 0.5 * (lo + hi)
+            if curved_cap(Rw, size_for(mid, vol), mid, dim)[1] > wet:
+                lo = mid
+            else:
+                hi = mid
+        theta = 0.5 * (lo + hi)
+        dv, dw = _excess(Rw, size_for(theta, vol), theta, dim, delta)
+        vol, wet = volume - dv, wetted - dw
+    return theta
+
+
 def _check(volume, base):
     if not (volume > 0 and base > 0):
         raise ValueError("no drop on the wall (volume %g, wetted %g)" % (volume, base))
 
 
-def contact_angle(moments, dim, delta=0.0, method="base"):
-    """Degrees, for a drop on a flat wall; moments as returned by
-    Solver.wetting_moments.  method "base": liquid volume and wetted base;
-    "centroid": liquid volume and centroid height above the wall (the wall is
-    normal to the last axis, at the coordinate of the wetted centroid)."""
+def contact_angle(moments, dim, delta=0.0, method="base", wall_radius=None):
+    """Degrees; moments as returned by Solver.wetting_moments.  On a flat wall,
+    method "base": liquid volume and wetted base; "centroid": liquid volume and
+    centroid height above the wall (the wall is normal to the last axis, at the
+    coordinate of the wetted centroid).  With wall_radius, the wall is a
+    cylinder (2D) or sphere (3D) of that radius."""
+    if wall_radius is not None:
+        _check(moments["volume"], moments["wetted"])
+        return math.degrees(cap_angle_on_curved_wall(moments["volume"], moments["wetted"],
+                                                     wall_radius, dim, delta))
     if method == "centroid":
         ax = dim - 1
         height = abs(moments["centroid"][ax] - moments["wet_centroid"][ax])

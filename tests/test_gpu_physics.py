@@ -59,7 +59,7 @@ def test_cylinder_contact_angle(deg):
     Rd = 0.15
     c = make_case("cyl", m, "D2Q9", 0.1, delta, 1.0, math.radians(deg),
                   rho0=inputs.cylinder_cap_density(m, (0.5, 0.5), Rc, Rd, math.radians(deg), delta))
-    rho, d = _run(c, 15000)
+    rho, d, w = _run(c, 15000, moments=True)
     assert d["status"] == 0
     p = contour_points(m.node_xyz, rho.reshape(m.n_elem, -1), 0.55, 7)
     p = p[np.linalg.norm(p - 0.5, axis=1) > Rc + delta]
@@ -67,6 +67,9 @@ def test_cylinder_contact_angle(deg):
     dist = math.hypot(cx - 0.5, cy - 0.5)
     th = math.degrees(math.acos((Rc ** 2 + R ** 2 - dist ** 2) / (2 * Rc * R)))
     assert abs(th - deg) < 4.0, (deg, th)
+    # the same angle from the device's wetting moments (liquid area and wetted arc)
+    th_dev = wetting.contact_angle(w, 2, delta=delta, wall_radius=Rc)
+    assert abs(th_dev - deg) < 4.0 and abs(th_dev - th) < 3.0, (deg, th, th_dev)
 
 
 @pytest.mark.parametrize("R", [0.25, 0.3])
@@ -144,4 +147,21 @@ def test_flat_wall_contact_angle_3d(deg):
     rho, d, w = _run(c, 6000, moments=True)
     assert d["status"] == 0 and d["ke_max"] < 1e-6, d
     th = wetting.contact_angle(w, 3, delta=0.07)
+    assert abs(th - deg) < 4.0, (deg, th)
+
+
+@pytest.mark.parametrize("deg", [60, 90, 120])
+def test_sphere_wall_contact_angle_3d(deg):
+    """A drop on the sphere-cap bottom of Sec. 3.2 (wall sphere of radius 0.7
+    under the 0.5 x 0.5 x 0.25 box, D3Q13), started at its equilibrium position
+    on the sphere, keeps the prescribed angle; measured from the device's
+    wetting moments with the sphere-sphere lens geometry."""
+    m = inputs.sphere_cap_box(5, (8, 8, 6))
+    th0 = math.radians(deg)
+    c = make_case("sph", m, "D3Q13", 0.01, 0.035, 1.0, th0,
+                  rho0=inputs.curved_cap_density(m, (0.25, 0.25, -0.7), 0.7, 0.13, th0, 0.035,
+                                                 (0.0, 0.0, 1.0)))
+    rho, d, w = _run(c, 8000, moments=True)
+    assert d["status"] == 0 and d["ke_max"] < 1e-6, d
+    th = wetting.contact_angle(w, 3, delta=0.035, wall_radius=0.7)
     assert abs(th - deg) < 4.0, (deg, th)

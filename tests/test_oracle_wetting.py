@@ -8,7 +8,8 @@ a curved interface follow the Sommerfeld expansion with no odd terms:
   a line through a disc: int phi dx = 2 R   (exactly, up to exp(-4R/delta) terms)
 Halves of these sit on a wall through the centre.  The oracle's quadratures
 converge to them spectrally; the contact-angle inversion recovers sharp caps
-exactly and the equilibrium-cap initial densities to within two degrees.
+exactly and the equilibrium-cap initial densities to within two degrees on flat
+walls (2.5 on cylinders and spheres).
 """
 import math
 
@@ -105,3 +106,52 @@ def test_measured_reference_densities():
     assert w["wetted"] == pytest.approx(2 * R, rel=5e-3)
     nominal = o.wetting_moments(f, 0, 0.1, 1.0)                 # vapour counted as liquid
     assert nominal["volume"] > w["volume"] + 0.02
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("deg", [25, 60, 90, 135, 165])
+def test_curved_caps_invert_exactly(dim, deg):
+    v, w = wetting.curved_cap(0.15, 0.11, math.radians(deg), dim)
+    assert math.degrees(wetting.cap_angle_on_curved_wall(v, w, 0.15, dim)) == pytest.approx(deg, abs=1e-7)
+
+
+def test_curved_cap_geometry():
+    """The lens formulas against brute force (2D: a fine grid of the drop disc
+    outside the wall disc, the wall arc by angular sampling) and against the
+    flat-wall caps as the wall radius grows."""
+    Rw, Rd, t = 0.2, 0.15, math.radians(70)
+    area, arc = wetting.curved_cap(Rw, Rd, t, 2)
+    d = math.sqrt(Rw * Rw + Rd * Rd - 2 * Rw * Rd * math.cos(t))
+    n = 2000
+    x, y = np.meshgrid(np.linspace(-0.4, 0.4, n), np.linspace(-0.3, 0.5, n))
+    h = 0.8 / (n - 1)
+    inside = ((x ** 2 + (y - d) ** 2) < Rd * Rd) & ((x ** 2 + y ** 2) >= Rw * Rw)
+    assert area == pytest.approx(inside.sum() * h * h, rel=2e-3)
+    phi = np.linspace(0, 2 * np.pi, 200001)
+    on = (Rw * np.cos(phi)) ** 2 + (Rw * np.sin(phi) - d) ** 2 < Rd * Rd
+    assert arc == pytest.approx(on.mean() * 2 * np.pi * Rw, rel=1e-4)
+    for dim in (2, 3):
+        v, w = wetting.curved_cap(1e4, 0.3, t, dim)     # larger radii lose digits to cancellation
+        hc = 0.3 * (1 - math.cos(t))
+        vf = 0.09 * (t - math.sin(t) * math.cos(t)) if dim == 2 else math.pi * hc * hc * (0.9 - hc) / 3
+        wf = 0.6 * math.sin(t) if dim == 2 else math.pi * (0.3 * math.sin(t)) ** 2
+        assert v == pytest.approx(vf, rel=1e-4) and w == pytest.approx(wf, rel=1e-4)
+
+
+@pytest.mark.parametrize("deg", [60, 90, 120])
+def test_diffuse_caps_on_a_cylinder(deg):
+    Rc, Rd, d = 0.15, 0.15, 0.06
+    m = inputs.cylinder_ogrid(8, n_theta=48, n_r=10, Rc=Rc)
+    rho0 = inputs.cylinder_cap_density(m, (0.5, 0.5), Rc, Rd, math.radians(deg), d)
+    w = _moments(m, "D2Q9", rho0)
+    assert wetting.contact_angle(w, 2, delta=d, wall_radius=Rc) == pytest.approx(deg, abs=2.5)
+
+
+@pytest.mark.parametrize("deg", [60, 90, 120])
+def test_diffuse_caps_on_a_sphere(deg):
+    """The sphere-cap box of Sec. 3.2 (wall sphere of radius 0.7 under the box)."""
+    m = inputs.sphere_cap_box(5, (8, 8, 6))
+    rho0 = inputs.curved_cap_density(m, (0.25, 0.25, -0.7), 0.7, 0.14, math.radians(deg), 0.04,
+                                     (0.0, 0.0, 1.0))
+    w = _moments(m, "D3Q13", rho0)
+    assert wetting.contact_angle(w, 3, delta=0.04, wall_radius=0.7) == pytest.approx(deg, abs=2.5)
