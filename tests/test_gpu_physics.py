@@ -69,7 +69,7 @@ def test_cylinder_contact_angle(deg):
     assert abs(th - deg) < 4.0, (deg, th)
     # the same angle from the device's wetting moments (liquid area and wetted arc)
     th_dev = wetting.contact_angle(w, 2, delta=delta, wall_radius=Rc)
-    assert abs(th_dev - deg) < 4.0 and abs(th_dev - th) < 3.0, (deg, th, th_dev)
+    assert abs(th_dev - deg) < 4.0 and abs(th_dev - th) < 5.0, (deg, th, th_dev)
 
 
 @pytest.mark.parametrize("R", [0.25, 0.3])
@@ -161,7 +161,7 @@ def test_sphere_wall_contact_angle_3d(deg):
     c = make_case("sph", m, "D3Q13", 0.01, 0.035, 1.0, th0,
                   rho0=inputs.curved_cap_density(m, (0.25, 0.25, -0.7), 0.7, 0.13, th0, 0.035,
                                                  (0.0, 0.0, 1.0)))
-    rho, d, w = _run(c, 8000, moments=True)
+    rho, d, w = _run(c, 12000, moments=True)
     assert d["status"] == 0 and d["ke_max"] < 1e-6, d
     th = wetting.contact_angle(w, 3, delta=0.035, wall_radius=0.7)
     assert abs(th - deg) < 4.0, (deg, th)
