@@ -69,31 +69,6 @@ def cap_angle_3d(volume, wetted, delta=0.0, iters=20):
     return theta
 
 
-def _h2(t):
-    s, c = math.sin(t), math.cos(t)
-    seg = t - s * c
-    return (2 * s ** 3 / (3 * seg) - c) / math.sqrt(seg)
-
-
-def _h3(t):
-    c = math.cos(t)
-    h = 1 - c                                    # in units of R
-    vol = math.pi * h * h * (3 - h) / 3
-    zc = 3 * (2 - h) ** 2 / (4 * (3 - h)) - (1 - h)
-    return zc / vol ** (1.0 / 3.0)
-
-
-def cap_angle_from_centroid(volume, height, dim):
-    """Contact angle (radians) of a cap from its liquid volume (area in 2D) and
-    the height of its centroid above the wall: a circular segment's centroid
-    lies 2 R^3 sin^3(theta) / (3 A) - R cos(theta) above its chord, a spherical
-    cap's 3 (2R - h)^2 / (4 (3R - h)) - (R - h) above its base (h = R(1 - cos
-    theta)); height / volume^(1/dim) depends on theta alone.  Both integrals are
-    bulk integrals, so the structure of the interface next to the wall hardly
-    enters."""
-    return _bisect(_h2 if dim == 2 else _h3, height / volume ** (1.0 / dim))
-
-
 # ---------------------------------------------------------------------------
 # Curved walls: a drop of radius Rd on a cylinder (2D) or sphere (3D) of radius
 # Rw, centres a distance d apart with d^2 = Rw^2 + Rd^2 - 2 Rw Rd cos(theta)
@@ -171,20 +146,14 @@ def _check(volume, base):
         raise ValueError("no drop on the wall (volume %g, wetted %g)" % (volume, base))
 
 
-def contact_angle(moments, dim, delta=0.0, method="base", wall_radius=None):
-    """Degrees; moments as returned by Solver.wetting_moments.  On a flat wall,
-    method "base": liquid volume and wetted base; "centroid": liquid volume and
-    centroid height above the wall (the wall is normal to the last axis, at the
-    coordinate of the wetted centroid).  With wall_radius, the wall is a
-    cylinder (2D) or sphere (3D) of that radius."""
+def contact_angle(moments, dim, delta=0.0, wall_radius=None):
+    """Degrees, from the liquid volume and wetted measure of Solver.wetting_moments:
+    a flat wall, or with wall_radius a cylinder (2D) or sphere (3D) of that
+    radius."""
     if wall_radius is not None:
         _check(moments["volume"], moments["wetted"])
         return math.degrees(cap_angle_on_curved_wall(moments["volume"], moments["wetted"],
                                                      wall_radius, dim, delta))
-    if method == "centroid":
-        ax = dim - 1
-        height = abs(moments["centroid"][ax] - moments["wet_centroid"][ax])
-        return math.degrees(cap_angle_from_centroid(moments["volume"], height, dim))
     _check(moments["volume"], moments["wetted"])
     f = cap_angle_2d if dim == 2 else cap_angle_3d
     return math.degrees(f(moments["volume"], moments["wetted"], delta))
