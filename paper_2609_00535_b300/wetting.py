@@ -1,5 +1,7 @@
-"""Static contact angle of a sessile drop on a flat wall from the wetting moments
-that the library integrates on the device (sem_lbm_wetting_moments).
+"""Static contact angle of a sessile drop from the wetting moments that the
+library integrates on the device (sem_lbm_wetting_moments): on a flat wall (the
+cap relations below) or on a circular cylinder / sphere (the lens geometry of
+curved_cap, further down).
 
 A drop at equilibrium on a flat wall is a circular cap (2D) or a spherical cap
 (3D) meeting the wall at the contact angle theta measured through the liquid
