@@ -105,3 +105,28 @@ def test_converging_request_stream():
         assert c.name.startswith("boxdrop2d") and c.lattice == "D2Q9" and c.theta_tag == ()
         assert (c.mesh.face_kind == 1).sum() == 4 * int(round(math.sqrt(r.E))) and c.dt > 1e-3
         assert abs(c.rho0.max() - c.rho_l) < 1e-3 and abs(c.rho0.min() - c.rho_v) < 1e-3
+
+
+def test_generator_defaults_match_the_paper():
+    """The workload generators default to the parameters the paper prints
+    (tests/golden/paper_values.json, each entry with its citation)."""
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+    iso, sph = gold["isolated_droplet"], gold["sphere"]
+    c = inputs.periodic_droplet()
+    assert (c.rho_l, c.rho_v) == (gold["densities"]["rho_l"], gold["densities"]["rho_v"])
+    assert c.tau == iso["tau"] and c.beta == iso["beta"] and c.mesh.N != 0
+    assert c.extra["R"] * 2 == iso["D"] and c.extra["delta"] == pytest.approx(iso["Cn"] * iso["D"])
+    assert np.ptp(c.mesh.node_xyz[..., 0]) == pytest.approx(iso["L"])
+    s = inputs.sphere_3d(ne=(2, 2, 2))
+    assert s.extra["La"] == sph["La"] and s.extra["delta"] == pytest.approx(sph["Cn"] * sph["drop_d"])
+    x = s.mesh.node_xyz.reshape(-1, 3)
+    assert np.ptp(x[:, 0]) == pytest.approx(sph["box"][0]) and np.ptp(x[:, 1]) == pytest.approx(sph["box"][1])
+    assert x[:, 2].max() == pytest.approx(sph["box"][2])
+    top = x[np.argmin(np.hypot(x[:, 0] - 0.25, x[:, 1] - 0.25))]          # sphere top under the drop
+    assert top[2] == pytest.approx(0.0, abs=1e-12)
+    n = s.mesh.N + 1
+    wall = s.mesh.node_xyz[s.mesh.face_kind[:, 4] == 1][:, :n * n].reshape(-1, 3)   # l = 0 face nodes
+    r = np.linalg.norm(wall - [0.25, 0.25, -sph["sphere_D"] / 2], axis=1)
+    assert len(wall) > 0 and np.allclose(r, sph["sphere_D"] / 2, atol=1e-12)
