@@ -333,6 +333,41 @@ def angle_sweep_section(args, device):
     return out
 
 
+def lattice_section(args, device):
+    """The sphere workload with the cubic velocity sets D3Q19 and D3Q27 (same mesh,
+    N and parameters): node-updates/s and the k_rhs FP64 roofline of each."""
+    import torch
+    from paper_2609_00535_b300 import semlbm
+    peak, _ = semlbm.fp64_peak_tflops(device)
+    out = {}
+    for lat in ("D3Q19", "D3Q27"):
+        case = inputs.sphere_3d(ne=(args.ne,) * 3 if args.ne else (16, 16, 16), lattice=lat)
+        s = semlbm.Solver.from_case(case, device=device)
+        s.set_density(case.rho0)
+        s.step(3)
+        s.synchronize()
+        s.profile(True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s.stream)
+        s.step(args.lattice_steps)
+        e1.record(s.stream)
+        s.synchronize()
+        ms = e0.elapsed_time(e1)
+        prof = s.profile_read()
+        s.profile(False)
+        info = s.info
+        rhs_ms = prof["ms"]["k_rhs"] / max(prof["launches"]["k_rhs"], 1)
+        work = flopcount.rhs_work(lat, case.mesh.N, info["n_local"], info["n_wall_nodes"])
+        ach = work["flops"] / (rhs_ms * 1e-3) / 1e12
+        out[lat] = {"node_updates_per_s": info["n_local"] * args.lattice_steps / (ms * 1e-3),
+                    "ms_per_step": ms / args.lattice_steps, "k_rhs_ms": rhs_ms,
+                    "k_rhs_tflops": ach, "k_rhs_frac": ach / peak,
+                    "status": s.diagnostics()["status"]}
+        s.close()
+    return out
+
+
 def native_arm(args):
     import numpy as np
     import torch
@@ -440,6 +475,7 @@ def native_arm(args):
         batched = serving = None
         if not args.no_batched:
             batched = batched_section(args, device)
+        lattices = None if args.no_lattices else lattice_section(args, device)
         serving_converge = sweep = None
         if not args.no_serving:
             cap = batched["batched_node_updates_per_s"] if batched else value
@@ -484,6 +520,7 @@ def native_arm(args):
             "serving": serving,
             "serving_to_convergence": serving_converge,
             "angle_sweep": sweep,
+            "lattices": lattices,
             "final_diag": {"ke_max": d["ke_max"], "mass": d["mass"], "status": d["status"]},
         }
         print(json.dumps(line), flush=True)
@@ -513,6 +550,8 @@ def main():
     ap.add_argument("--converge-requests", type=int, default=100)
     ap.add_argument("--converge-rate", type=float, default=20.0)
     ap.add_argument("--sweep-requests", type=int, default=32)
+    ap.add_argument("--lattice-steps", type=int, default=50)
+    ap.add_argument("--no-lattices", action="store_true", help="skip the D3Q19/D3Q27 lines")
     ap.add_argument("--sweep-max-steps", type=int, default=100000)
     ap.add_argument("--ne", type=int, default=None,
                     help="elements per axis of the sphere-cap mesh (profiling cases only)")
