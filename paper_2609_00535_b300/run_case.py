@@ -2,6 +2,7 @@
 
   python -m paper_2609_00535_b300.run_case --case flat2d --steps 300000 --every 5000
   python -m paper_2609_00535_b300.run_case --case droplet2d --N 8 --ne 4 --cfl 0.2 ...
+  python -m paper_2609_00535_b300.run_case --case capwall2d --theta 60 --steps 300000
 
 Prints one JSON line per case: time step, wall time per step, and KE_max at
 evenly spaced checkpoints (stops early on a non-finite state).
@@ -25,6 +26,9 @@ def make(args):
     if args.case == "sphere3d":
         ne = (args.ne,) * 3 if args.ne else (16, 16, 16)
         return inputs.sphere_3d(N=args.N or 5, ne=ne, theta=math.radians(args.theta), cfl=args.cfl)
+    if args.case == "capwall2d":      # stiff flat-wall drop started at its equilibrium cap
+        return inputs.cap_on_wall_2d(math.radians(args.theta), N=args.N or 4, ne=args.ne or 8,
+                                     cfl=args.cfl)
     if args.case in ("droplet2d", "droplet3d"):
         dim = 2 if args.case == "droplet2d" else 3
         if args.beta:
