@@ -666,10 +666,11 @@ __device__ __forceinline__ void body_dss_rk(const View& v, const double* gcur, d
 }
 
 // resident CTAs per SM the streaming kernel is compiled for (register cap)
-// (three CTAs of up to 256 threads; larger tiles keep the compiler's choice)
+// (four CTAs of up to 256 threads, 72 registers; larger tiles keep the
+// compiler's choice)
 template <int D, int NP, int EPB>
 constexpr int rhs_min_blocks() {
-  return cta_threads<D, NP, EPB>() <= 256 ? 3 : 1;
+  return cta_threads<D, NP, EPB>() <= 256 ? 4 : 1;
 }
 
 // ---------------------------------------------------------------------------
