@@ -275,6 +275,11 @@ typedef struct {
 
 /* stream: cudaStream_t or NULL for a batch-owned stream. */
 int sem_lbm_batch_create(void* stream, sem_lbm_batch_t** out);
+/* The stream the batch steps on (the one given to sem_lbm_batch_create, or the
+ * batch's own when that was NULL); NULL for a NULL batch.  A batch captures its
+ * step into a CUDA graph on this stream, so no other thread may use the stream
+ * meanwhile: give each batch a stream of its own. */
+void* sem_lbm_batch_stream(const sem_lbm_batch_t* b);
 /* Adds s (state set, same device, N <= 8); returns its slot index. */
 int sem_lbm_batch_add(sem_lbm_batch_t* b, sem_lbm_t* s, int* slot);
 /* Removes the solver in `slot` (after the batch's pending work). */

@@ -552,6 +552,8 @@ void sem_lbm_batch_destroy(sem_lbm_batch_t* b) {
   delete b;
 }
 
+void* sem_lbm_batch_stream(const sem_lbm_batch_t* b) { return b ? (void*)b->stream : nullptr; }
+
 int sem_lbm_batch_slot_of(const sem_lbm_t* s) {
   if (!s || !s->batch) return -1;
   for (size_t i = 0; i < s->batch->slots.size(); ++i)

@@ -27,7 +27,8 @@ EXPORTED = ["sem_lbm_workspace_bytes", "sem_lbm_create", "sem_lbm_set_density", 
             "sem_lbm_profile_read", "sem_lbm_chemical_potential_noalloc",
             "sem_lbm_batch_create", "sem_lbm_batch_add", "sem_lbm_batch_remove",
             "sem_lbm_batch_step", "sem_lbm_batch_tune", "sem_lbm_batch_diagnostics",
-            "sem_lbm_batch_info", "sem_lbm_batch_slot_of", "sem_lbm_batch_destroy"]
+            "sem_lbm_batch_info", "sem_lbm_batch_slot_of", "sem_lbm_batch_stream",
+            "sem_lbm_batch_destroy"]
 NOALLOC_MAX_NODES = 1 << 20
 KERNEL_CLASSES = ["k_lap", "k_dss_mu", "k_force", "k_dss_collide", "k_rhs", "k_dss_rk"]
 PEAK_PATH = os.path.join(_HERE, "libsemlbm_peak.so")
@@ -133,6 +134,8 @@ def load():
     L.sem_lbm_batch_diagnostics.argtypes = [P, ctypes.POINTER(DiagC), I]
     L.sem_lbm_batch_info.argtypes = [P, ctypes.POINTER(GroupInfoC), I, ctypes.POINTER(I)]
     L.sem_lbm_batch_slot_of.argtypes = [P]
+    L.sem_lbm_batch_stream.argtypes = [P]
+    L.sem_lbm_batch_stream.restype = P
     L.sem_lbm_batch_destroy.argtypes = [P]
     L.sem_lbm_batch_destroy.restype = None
     for name in ("sem_lbm_batch_create", "sem_lbm_batch_add", "sem_lbm_batch_remove",
@@ -335,13 +338,18 @@ class Batch:
     """Several solves stepped together (see sem_lbm_batch_* in sem_lbm.h)."""
 
     def __init__(self, stream=None, device=0):
+        # without a caller stream the batch uses one the library creates for it:
+        # torch's pooled streams repeat, and a solver built on another thread on
+        # the same stream would collide with the batch's graph capture
         import torch
         self.device = torch.device("cuda", device)
-        self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
-            check(load().sem_lbm_batch_create(self.stream.cuda_stream, ctypes.byref(h)))
+            check(load().sem_lbm_batch_create(stream.cuda_stream if stream is not None else None,
+                                              ctypes.byref(h)))
         self.h = h
+        self.stream = stream if stream is not None else torch.cuda.ExternalStream(
+            load().sem_lbm_batch_stream(h), device=self.device)
         self.members = {}
 
     def add(self, solver):

@@ -162,3 +162,21 @@ def test_batch_with_moving_wall_member():
     b.close()
     for s in solvers:
         s.close()
+
+
+def test_batch_stream_is_not_shared_with_solvers():
+    """A batch captures its step on its stream; solvers created meanwhile (on
+    other threads, from torch's stream pool, which repeats) never get that stream."""
+    import torch
+    from paper_2609_00535_b300 import semlbm
+    b = semlbm.Batch()
+    pooled = {torch.cuda.Stream().cuda_stream for _ in range(80)}
+    assert b.stream.cuda_stream not in pooled
+    s = _solver(inputs.flat_wall_2d())
+    b.add(s)
+    b.step(3)
+    b.synchronize()
+    f, k = s.get_state()
+    assert k == 3 and np.array_equal(f, alone(inputs.flat_wall_2d(), 3))
+    b.close()
+    s.close()
