@@ -37,6 +37,10 @@
  *   - Calls on one solver are not thread safe; distinct solvers are
  *     independent.  Work is enqueued on the solver's stream (params.stream,
  *     else a stream the solver owns).
+ *   - A solver (and a batch) lives on the device that was current when it was
+ *     created.  Every later call makes that device current for its own
+ *     duration and restores the caller's current device before returning, so
+ *     callers that switch devices need not switch back first.
  */
 #ifndef SEM_LBM_H
 #define SEM_LBM_H
@@ -132,6 +136,11 @@ typedef struct {
   size_t workspace_bytes;
   int graph_launches;        /* 1 if steps replay a captured CUDA graph         */
   int kernels_per_step;      /* kernel launches in one time step                */
+  int elements_per_cta;      /* elements per CTA of the element kernels         */
+  int rhs_pair_groups;       /* CTAs that share the velocity pairs of one element
+                                batch in the streaming right-hand side: 1 = one
+                                CTA per element batch (meshes that fill the GPU),
+                                > 1 = the pair-split form for small meshes      */
 } sem_lbm_info_t;
 
 /* Device bytes sem_lbm_create needs for this mesh (for admission control and

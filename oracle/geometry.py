@@ -17,10 +17,14 @@ element, global node ids, face kinds and tags):
 * direct-stiffness summation: copies with the same global id are summed with
   numpy's ``bincount`` (sequential accumulation) and the sum is scattered back.
 
-Pinned by tests/test_oracle_geometry.py: sum of M_e equals the area/volume of
-affine meshes exactly and converges spectrally on curved meshes, the area
-vector equals det J times the matching row of J^-1, the discrete area vectors of
-a closed wall sum to zero, and the gather-scatter against a dense assembly.
+Pinned by tests/test_oracle_operators.py: sum of M_e equals the area/volume of
+affine meshes exactly and converges spectrally on curved meshes
+(test_areas_and_volumes), the area vector equals det J times the matching row
+of J^-1 (test_area_vector_is_cofactor_row), the discrete area vectors of a
+closed wall sum to zero (test_closed_wall_area_vectors_sum_to_zero), wall nodes
+lie on the curved walls, and the mass matrix and gather-scatter against the
+independent dense assembly of tests/brute_dense.py (test_mass_matrix_dense,
+test_dss_counts_shared_copies).
 """
 import numpy as np
 

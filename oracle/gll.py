@@ -11,9 +11,9 @@ Route taken here (deliberately different from the CUDA library's host tables):
 * derivative matrix: D_ij = l_j'(x_i) from the generic product formula for the
   derivative of a Lagrange polynomial (no GLL-specific closed form).
 
-Pinned by tests/test_oracle_gll.py: closed forms for N = 2 and N = 4, exactness
-of the quadrature to degree 2N-1 and of D on polynomials of degree <= N, and a
-cross-check of the nodes against numpy's Legendre root finder.
+Pinned by tests/test_oracle_tables.py (test_gll_*): closed forms for N = 2 and
+N = 4, exactness of the quadrature to degree 2N-1 and of D on polynomials of
+degree <= N, and a cross-check of the nodes against numpy's Legendre root finder.
 """
 import numpy as np
 

@@ -8,7 +8,8 @@
   the 13-point degree-5 quadrature of the Maxwellian; the spectral element
   streaming does not require lattice-conforming velocities.
 
-Pinned by tests/test_oracle_lattice.py: the weight moments sum(t) = 1,
+Pinned by tests/test_oracle_tables.py (test_velocity_set_moments,
+test_d3q13_speed): the weight moments sum(t) = 1,
 sum(t e) = 0, sum(t e e) = c_s^2 I, odd moments zero to rank 5 and the rank-4
 isotropic tensor c_s^4 (dd + dd + dd), plus closure of the set under e -> -e.
 """

@@ -34,10 +34,14 @@ stated; they are the same readings the CUDA library implements):
  * Wall velocity u_b per wall tag (static, u_b = 0, unless given); tags < 0
    are static neutral walls.
 
-Pinned by tests/test_oracle_method.py and tests/test_oracle_brute.py (dense
-brute-force assembly on 1-4 element meshes, stationarity, mass conservation,
-equilibrium moments, the tanh interface, tilted-interface wetting residual,
-RK3 on a linear ODE).
+Pinned by tests/test_oracle_operators.py (dense brute-force assembly of
+tests/brute_dense.py on 1-4 element meshes: weak Laplacian with the wetting
+term, force average, streaming right-hand side with bounce-back),
+tests/test_oracle_physics.py (stationarity, mass conservation, the tanh
+interface, tilted-interface wetting residual, collision moments, Couette flow),
+tests/test_oracle_tables.py (equilibrium and force moments, mu0 = de0/drho,
+RK3 on a linear ODE), tests/test_oracle_equilibria.py (Laplace law, static
+angle) and tests/test_oracle_wetting.py (wetting moments).
 """
 import numpy as np
 

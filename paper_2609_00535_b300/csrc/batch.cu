@@ -321,6 +321,7 @@ int sem_lbm_batch_add(sem_lbm_batch_t* b, sem_lbm_t* s, int* slot) {
   if (s->batch) return fail(SEMLBM_EINVAL, "solver already belongs to a batch");
   if (!s->state_ready) return fail(SEMLBM_EINVAL, "solver state not set");
   if (s->device != b->device) return fail(SEMLBM_EINVAL, "solver and batch are on different devices");
+  DeviceGuard dg(b->device);
   if (s->N > kBatchMaxN) return fail(SEMLBM_EUNSUPPORTED, "batched kernels are built for N <= %d", kBatchMaxN);
   BatchGroup* g = nullptr;
   for (BatchGroup* x : b->groups)
@@ -377,6 +378,7 @@ int sem_lbm_batch_add(sem_lbm_batch_t* b, sem_lbm_t* s, int* slot) {
 int sem_lbm_batch_remove(sem_lbm_batch_t* b, int slot) {
   if (!b || slot < 0 || slot >= (int)b->slots.size() || !b->slots[slot])
     return fail(SEMLBM_EINVAL, "no solver in slot %d", slot);
+  DeviceGuard dg(b->device);
   CUDA_TRY(cudaStreamSynchronize(b->stream));
   sem_lbm* s = b->slots[slot];
   for (size_t gi = 0; gi < b->groups.size(); ++gi) {
@@ -401,6 +403,7 @@ int sem_lbm_batch_remove(sem_lbm_batch_t* b, int slot) {
 
 int sem_lbm_batch_step(sem_lbm_batch_t* b, int64_t n_steps) {
   if (!b) return fail(SEMLBM_EINVAL, "NULL batch");
+  DeviceGuard dg(b->device);
   if (n_steps < 0) return fail(SEMLBM_EINVAL, "n_steps must be >= 0");
   if (b->groups.empty() || n_steps == 0) return 0;
   if (b->dirty || !b->graph) {
@@ -425,6 +428,7 @@ int sem_lbm_batch_step(sem_lbm_batch_t* b, int64_t n_steps) {
 
 int sem_lbm_batch_tune(sem_lbm_batch_t* b, int steps_per_candidate) {
   if (!b) return fail(SEMLBM_EINVAL, "NULL batch");
+  DeviceGuard dg(b->device);
   if (steps_per_candidate < 2) return fail(SEMLBM_EINVAL, "steps_per_candidate must be >= 2");
   cudaEvent_t e0, e1;
   CUDA_TRY(cudaEventCreate(&e0));
@@ -479,6 +483,7 @@ int sem_lbm_batch_tune(sem_lbm_batch_t* b, int steps_per_candidate) {
 
 int sem_lbm_batch_diagnostics(sem_lbm_batch_t* b, sem_lbm_diag* out, int n) {
   if (!b || (!out && n > 0)) return fail(SEMLBM_EINVAL, "NULL argument");
+  DeviceGuard dg(b->device);
   std::vector<DiagPart> parts(n);
   std::vector<int> flags(2 * n, 0);
   for (int i = 0; i < n; ++i) {
@@ -542,6 +547,7 @@ int sem_lbm_batch_info(sem_lbm_batch_t* b, sem_lbm_batch_group_info* out, int ma
 
 void sem_lbm_batch_destroy(sem_lbm_batch_t* b) {
   if (!b) return;
+  DeviceGuard dg(b->device);
   if (b->stream) cudaStreamSynchronize(b->stream);
   for (size_t i = 0; i < b->slots.size(); ++i)
     if (b->slots[i]) sem_lbm_batch_remove(b, (int)i);

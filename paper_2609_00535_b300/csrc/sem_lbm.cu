@@ -307,12 +307,17 @@ struct Impl {
   static void collide(sem_lbm& s) {
     k_dss_collide<L><<<grid_of(s.G, kDssThreads), kDssThreads, 0, s.stream>>>(s.view);
   }
-  static void rhs(sem_lbm& s, const double* gst) {
-    // small meshes: split the velocity pairs over up to NREP CTAs per element
-    // batch until the grid reaches two CTAs per SM
+  // small meshes: split the velocity pairs over up to NREP CTAs per element
+  // batch until the grid reaches two CTAs per SM (1 = the unsplit kernel)
+  static int rhs_split(const sem_lbm& s) {
     const int nb = blocks(s);
     int P = 1;
     while (P < L::NREP && (int64_t)nb * P < 2 * (int64_t)s.n_sm) ++P;
+    return P;
+  }
+  static void rhs(sem_lbm& s, const double* gst) {
+    const int nb = blocks(s);
+    const int P = rhs_split(s);
     if (P == 1)
       k_rhs<L, NP, EPB, false><<<nb, THREADS, SM_RHS, s.stream>>>(s.view, gst);
     else
@@ -355,7 +360,7 @@ struct Impl {
   }
   static Ops* ops() {
     static Ops o{geom, wallsetup, lap, mu, force, rhs, collide, rk, diag, init, density, velocity, prepare,
-                 lap_into, mu_from, wet};
+                 lap_into, mu_from, wet, rhs_split, EPB};
     return &o;
   }
 };
@@ -638,6 +643,7 @@ int sem_lbm_create(const sem_lbm_mesh* mesh, int N, sem_lbm_lattice lattice, dou
 
 int sem_lbm_set_density(sem_lbm_t* s, const double* rho, int on_device) {
   if (!s || !rho) return fail(SEMLBM_EINVAL, "NULL argument");
+  DeviceGuard dg(s->device);
   double* src = s->lapr;   // staging for host data (overwritten by the next step anyway)
   if (int rc = host_copy_in(s, src, rho, sizeof(double) * s->V, on_device)) return rc;
   CUDA_TRY(cudaMemsetAsync(s->flags, 0, 8 * sizeof(int), s->stream));
@@ -650,6 +656,7 @@ int sem_lbm_set_density(sem_lbm_t* s, const double* rho, int on_device) {
 
 int sem_lbm_set_state(sem_lbm_t* s, const double* fbar, int on_device, int64_t step) {
   if (!s || !fbar) return fail(SEMLBM_EINVAL, "NULL argument");
+  DeviceGuard dg(s->device);
   if (int rc = host_copy_in(s, s->f, fbar, sizeof(double) * s->Q * s->V, on_device)) return rc;
   s->ops->density(*s);
   CUDA_TRY(cudaGetLastError());
@@ -664,6 +671,7 @@ int sem_lbm_step(sem_lbm_t* s, int64_t n_steps) {
   if (!s->state_ready) return fail(SEMLBM_EINVAL, "state not set (call sem_lbm_set_density)");
   if (s->batch) return fail(SEMLBM_EINVAL, "solver is stepped by its batch (sem_lbm_batch_step)");
   if (n_steps == 0) return 0;
+  DeviceGuard dg(s->device);
   if (s->prof_on) {
     if (s->nev == 0 && !record_event(*s, -1)) return fail(SEMLBM_ECUDA, "cudaEventRecord failed");
     for (int64_t i = 0; i < n_steps; ++i) enqueue_step(*s);
@@ -691,6 +699,7 @@ int sem_lbm_step(sem_lbm_t* s, int64_t n_steps) {
 
 int sem_lbm_diagnostics(sem_lbm_t* s, sem_lbm_diag* out) {
   if (!s || !out) return fail(SEMLBM_EINVAL, "NULL argument");
+  DeviceGuard dg(s->device);
   if (!s->state_ready) return fail(SEMLBM_EINVAL, "state not set");
   s->ops->diag(*s);
   CUDA_TRY(cudaGetLastError());
@@ -715,6 +724,7 @@ int sem_lbm_diagnostics(sem_lbm_t* s, sem_lbm_diag* out) {
 int sem_lbm_wetting_moments(sem_lbm_t* s, int tag, double rho_v_ref, double rho_l_ref,
                             sem_lbm_wetting* out) {
   if (!s || !out) return fail(SEMLBM_EINVAL, "NULL argument");
+  DeviceGuard dg(s->device);
   if (!s->state_ready) return fail(SEMLBM_EINVAL, "state not set");
   WetPart w;
   if (!(rho_v_ref > 0) || !(rho_l_ref > 0)) {
@@ -753,6 +763,7 @@ int sem_lbm_wetting_moments(sem_lbm_t* s, int tag, double rho_v_ref, double rho_
 
 int sem_lbm_get_field(sem_lbm_t* s, int which, double* dst, int dst_on_device) {
   if (!s || !dst) return fail(SEMLBM_EINVAL, "NULL argument");
+  DeviceGuard dg(s->device);
   if (!s->state_ready) return fail(SEMLBM_EINVAL, "state not set");
   const double* src;
   size_t count;
@@ -793,6 +804,8 @@ int sem_lbm_get_info(const sem_lbm_t* s, sem_lbm_info_t* out) {
   out->workspace_bytes = s->ws_bytes;
   out->graph_launches = 1;
   out->kernels_per_step = s->kernels_per_step;
+  out->elements_per_cta = s->ops->epb;
+  out->rhs_pair_groups = s->ops->rhs_split(*s);
   return 0;
 }
 
@@ -805,6 +818,7 @@ int sem_lbm_profile(sem_lbm_t* s, int enable) {
 
 int sem_lbm_profile_read(sem_lbm_t* s, sem_lbm_profile_t* out) {
   if (!s || !out) return fail(SEMLBM_EINVAL, "NULL argument");
+  DeviceGuard dg(s->device);
   memset(out, 0, sizeof *out);
   CUDA_TRY(cudaStreamSynchronize(s->stream));
   for (size_t i = 1; i < s->nev; ++i) {
@@ -866,6 +880,7 @@ int sem_lbm_chemical_potential_noalloc(sem_lbm_t* s, const double* rho, double* 
     return fail(SEMLBM_EINVAL,
                 "mesh has %lld element-local nodes; the allocation-free entry point holds at most %d",
                 (long long)s->V, SEMLBM_NOALLOC_MAX_NODES);
+  DeviceGuard dg(s->device);
   double* scratch = nullptr;
   if (int rc = noalloc_scratch(s->device, &scratch)) return rc;
   // k_lap writes every one of the V partials it then reads: nothing to clear
@@ -877,6 +892,7 @@ int sem_lbm_chemical_potential_noalloc(sem_lbm_t* s, const double* rho, double* 
 
 void sem_lbm_destroy(sem_lbm_t* s) {
   if (!s) return;
+  DeviceGuard dg(s->device);
   if (s->batch) sem_lbm_batch_remove(s->batch, sem_lbm_batch_slot_of(s));
   if (s->stream) cudaStreamSynchronize(s->stream);
   for (cudaEvent_t e : s->ev) cudaEventDestroy(e);

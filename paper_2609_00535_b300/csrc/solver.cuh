@@ -19,6 +19,26 @@ constexpr int kDssThreads = 128;   // threads per CTA of the gather-scatter kern
 
 inline int grid_of(int64_t work, int threads) { return (int)((work + threads - 1) / threads); }
 
+// Makes `device` current for the lifetime of the guard and restores the
+// caller's device afterwards, so that a call on a solver or batch launches on
+// the device the object was created on, whatever device the caller has current.
+class DeviceGuard {
+ public:
+  explicit DeviceGuard(int device) {
+    if (cudaGetDevice(&prev_) == cudaSuccess && prev_ != device && cudaSetDevice(device) == cudaSuccess)
+      switched_ = true;
+  }
+  ~DeviceGuard() {
+    if (switched_) cudaSetDevice(prev_);
+  }
+  DeviceGuard(const DeviceGuard&) = delete;
+  DeviceGuard& operator=(const DeviceGuard&) = delete;
+
+ private:
+  int prev_ = 0;
+  bool switched_ = false;
+};
+
 }  // namespace semlbm
 
 #define CUDA_TRY(expr)                                                                      \
@@ -84,5 +104,7 @@ struct Ops {
   void (*lap_into)(sem_lbm&, const double* rho, double* partial);
   void (*mu_from)(sem_lbm&, const double* partial, const double* rho, double* mu);
   void (*wet)(sem_lbm&, int tag, double rho_v_ref, double rho_l_ref);
+  int (*rhs_split)(const sem_lbm&);   // CTAs sharing one element batch's velocity pairs
+  int epb;                            // elements per CTA of the element kernels
 };
 

@@ -15,6 +15,9 @@ import time
 from . import inputs, semlbm
 
 
+CASES = ("flat2d", "cylinder2d", "sphere3d", "capwall2d", "droplet2d", "droplet3d")
+
+
 def make(args):
     kw = {}
     if args.case == "flat2d":
@@ -41,7 +44,7 @@ def make(args):
     raise SystemExit("unknown case " + args.case)
 
 
-def main():
+def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--case", default="flat2d")
     ap.add_argument("--steps", type=int, default=100000)
@@ -55,7 +58,18 @@ def main():
     ap.add_argument("--Cn", type=float, default=None, help="interface width / diameter (droplets)")
     ap.add_argument("--force-split", type=int, default=0,
                     help="force in F**: 0 c_s^2 grad rho - rho grad mu, 1 -rho grad mu")
-    args = ap.parse_args()
+    args = ap.parse_args(argv)
+    if args.case not in CASES:
+        ap.error("unknown case %s (one of %s)" % (args.case, ", ".join(CASES)))
+    if args.force_split not in (0, 1):
+        ap.error("--force-split must be 0 or 1")
+    if args.steps <= 0 or args.every <= 0:
+        ap.error("--steps and --every must be positive")
+    return args
+
+
+def main(argv=None):
+    args = parse_args(argv)
     case = make(args)
     case.force_split = args.force_split
     s = semlbm.Solver.from_case(case)

@@ -31,3 +31,22 @@ def make_case(name, mesh, lattice, beta, delta, tau, theta_w, theta_tag=(), rho0
     dt = inputs.cfl_dt(mesh, lattice, cfl, kappa, rho_l)
     return inputs.Case(name, mesh, lattice, rho_l, rho_v, beta, kappa, tau, dt, theta_w,
                        tuple(theta_tag), rho0, wall_velocity=dict(wall_velocity or {}))
+
+
+def oracle_state(case, steps):
+    """fbar [Q, V] after `steps` oracle steps from the case's initial density."""
+    om, orc = oracle_of(case)
+    f = orc.initial_state(case.rho0.reshape(om.shape))
+    f = orc.run(f, steps)
+    return f.reshape(f.shape[0], -1)
+
+
+def assert_matches_oracle(case, f_gpu, steps, tol=1e-12):
+    """max |f_gpu - f_oracle| / max |f_oracle| <= tol, for fbar and rho."""
+    f_ref = oracle_state(case, steps)
+    f_gpu = np.asarray(f_gpu).reshape(f_ref.shape)
+    err = np.abs(f_gpu - f_ref).max() / np.abs(f_ref).max()
+    rho_ref = f_ref.sum(0)
+    err_rho = np.abs(f_gpu.sum(0) - rho_ref).max() / np.abs(rho_ref).max()
+    assert err <= tol and err_rho <= tol, (case.name, err, err_rho)
+    return err

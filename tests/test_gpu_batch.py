@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 from paper_2609_00535_b300 import inputs
-from tests.helpers import make_case
+from tests.helpers import assert_matches_oracle, make_case
 
 pytestmark = pytest.mark.gpu
 
@@ -58,6 +58,28 @@ def test_batch_matches_alone_bitwise():
     d = b.diagnostics()
     for slot, s in zip(slots, solvers):
         assert d[slot]["status"] == 0 and d[slot]["step"] == 25
+    b.close()
+    for s in solvers:
+        s.close()
+
+
+def test_batch_members_match_oracle():
+    """Members of four (velocity set, N) groups, advanced only by the batched
+    persistent kernels, element by element against the oracle."""
+    from paper_2609_00535_b300 import semlbm
+    cases = [inputs.flat_wall_2d(N=6, ne=(4, 4), theta=math.radians(75)),
+             inputs.sphere_3d(N=4, ne=(3, 3, 2), Cn=0.3, theta=math.radians(45)),
+             inputs.sphere_3d(N=5, ne=(2, 2, 2), Cn=0.35, theta=math.radians(120)),
+             inputs.periodic_droplet(dim=2, ne=3, N=8, Cn=0.25)]
+    b = semlbm.Batch()
+    solvers = [_solver(c) for c in cases]
+    for s in solvers:
+        b.add(s)
+    b.step(60)
+    for c, s in zip(cases, solvers):
+        f, k = s.get_state()
+        assert k == 60
+        assert_matches_oracle(c, f, 60)
     b.close()
     for s in solvers:
         s.close()

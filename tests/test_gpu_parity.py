@@ -35,8 +35,10 @@ def _rel(a, b):
     return np.abs(a - b).max() / np.abs(b).max()
 
 
-def _compare(case, steps, tol=TOL):
+def _compare(case, steps, tol=TOL, rhs_pair_groups=None):
     s = _solver(case)
+    if rhs_pair_groups is not None:      # which k_rhs variant the step launches
+        assert s.info["rhs_pair_groups"] == rhs_pair_groups, s.info
     s.step(steps)
     f_gpu, step = s.get_state()
     assert step == steps
@@ -72,6 +74,31 @@ def test_curved_rotated_cylinder_mesh():
 def test_sphere_3d_small():
     case = inputs.sphere_3d(N=4, ne=(3, 3, 2), Cn=0.3)
     _compare(case, 100)
+
+
+def test_sphere_cap_d3q13_1000_steps():
+    """The 3D case of Sec. 3.2 (sphere-cap wall at 60 degrees, D3Q13) on 18 curved
+    hexes at N = 4, held to 1e-12 relative after 1000 steps."""
+    case = inputs.sphere_3d(N=4, ne=(3, 3, 2), Cn=0.3)
+    _compare(case, 1000)
+
+
+def test_unsplit_rhs_kernel_against_oracle():
+    """320 hexes at N = 5 give more element batches than two per SM, so the
+    single-solve step launches k_rhs with one CTA per element batch: the kernel
+    variant that the sphere benchmark times (the smaller meshes above take the
+    pair-split variant)."""
+    case = inputs.sphere_3d(N=5, ne=(8, 8, 5))
+    _compare(case, 20, rhs_pair_groups=1)
+
+
+def test_benchmark_workload_full_size():
+    """The benchmark's own sphere workload (16^3 curved hexes, N = 5, D3Q13,
+    884,736 element-local nodes) in the launch configuration bench.py times,
+    element by element against the oracle for two steps."""
+    case = inputs.sphere_3d()
+    assert case.nodes == 884736
+    _compare(case, 2, rhs_pair_groups=1)
 
 
 @pytest.mark.parametrize("dim,N,ne", [(2, 8, 4), (3, 4, 2)])

@@ -7,6 +7,7 @@ import pytest
 
 from paper_2609_00535_b300 import inputs
 from paper_2609_00535_b300.serve import Server
+from tests.helpers import assert_matches_oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -30,6 +31,21 @@ def test_continuous_batching_equals_alone():
         s.step(rec.steps)
         assert np.array_equal(s.get_state()[0], rec.state), rec.name
         s.close()
+
+
+def test_served_requests_match_oracle():
+    """Requests served side by side (three kinds, three orders), each result
+    element by element against the oracle run of the same request."""
+    kinds = ["flat2d", "sphere3d", "droplet2d"]
+    reqs = [inputs.Request(i, 0.02 * i, k, 27 if "3d" in k else 36, 4 + i, math.radians(40 + 35 * i),
+                           1.0, 77 + i) for i, k in enumerate(kinds)]
+    srv = Server(hbm_budget_bytes=2 << 30, epoch_steps=20, ke_tol=0.0, max_steps=80,
+                 min_steps=20, keep_state=True, workers=3)
+    st = srv.run(reqs)
+    assert st.summary()["completed"] == len(reqs)
+    for req, rec in zip(reqs, st.records):
+        assert rec.steps >= 80 and rec.state is not None
+        assert_matches_oracle(req.case(), rec.state, rec.steps)
 
 
 def test_budget_limits_concurrent_slots():
