@@ -5,11 +5,15 @@
 // tiles of every field a kernel reads (rho, mu, the Q-1 moving f_alpha) and
 // the GLL derivative matrix are staged in shared memory, and each thread
 // applies the tensor-product (sum-factorised) derivative along each reference
-// axis with its rows of D held in registers.
+// axis, with its rows of D held in registers (k_lap, k_force) or read from
+// shared memory at each use (k_rhs, whose velocity loop would otherwise spill).
 //
 // Gather-scatter kernels (k_dss_*): one thread per global node group; the
 // copies of a shared node are summed in a fixed order (ascending local index),
-// so results do not depend on scheduling.
+// so results do not depend on scheduling.  The streaming partials that k_rhs
+// hands to k_dss_rk are node-major (the Q-1 values of a node contiguous, in
+// opposite-velocity pairs), so each copy of a node is gathered with 16-byte
+// loads from consecutive addresses.
 //
 // B300's FP64 pipe (about 1.1 TFLOP/s, measured) is the bound of this step, so
 // the formulation minimises FP64 instructions: velocity contractions use only
@@ -57,26 +61,33 @@ __device__ __forceinline__ void grad_ref(const double (&Dr)[D][NP], const NodeId
   if constexpr (D == 3) out[2] = dline<NP, NP * NP>(Dr[2], tile + k - ix.i[2] * NP * NP);
 }
 
-// reference gradients of two tiles at node k, as 2D independent chains
+// reference gradients of two tiles at node k, as 2D independent chains, with
+// the rows of D read from shared memory at every use (sD + i_b NP for axis b):
+// holding them in registers across the streaming kernel's velocity loop made
+// it spill
+__device__ __forceinline__ double lds(const double* p) { return *(volatile const double*)p; }
+
 template <int D, int NP>
-__device__ __forceinline__ void grad_ref2(const double (&Dr)[D][NP], const NodeIdx<D, NP>& ix,
-                                          const double* __restrict__ ta,
-                                          const double* __restrict__ tb, int k, double (&oa)[D],
-                                          double (&ob)[D]) {
+__device__ __forceinline__ void grad_ref2(const double* sD, const NodeIdx<D, NP>& ix,
+                                            const double* __restrict__ ta,
+                                            const double* __restrict__ tb, int k, double (&oa)[D],
+                                            double (&ob)[D]) {
   constexpr int st[3] = {1, NP, NP * NP};
   int k0[D];
 #pragma unroll
   for (int b = 0; b < D; ++b) {
     k0[b] = k - ix.i[b] * st[b];
-    oa[b] = Dr[b][0] * ta[k0[b]];
-    ob[b] = Dr[b][0] * tb[k0[b]];
+    const double d0 = lds(sD + ix.i[b] * NP);
+    oa[b] = d0 * ta[k0[b]];
+    ob[b] = d0 * tb[k0[b]];
   }
 #pragma unroll
   for (int m = 1; m < NP; ++m)
 #pragma unroll
     for (int b = 0; b < D; ++b) {
-      oa[b] = fma(Dr[b][m], ta[k0[b] + m * st[b]], oa[b]);
-      ob[b] = fma(Dr[b][m], tb[k0[b] + m * st[b]], ob[b]);
+      const double dm = lds(sD + ix.i[b] * NP + m);
+      oa[b] = fma(dm, ta[k0[b] + m * st[b]], oa[b]);
+      ob[b] = fma(dm, tb[k0[b] + m * st[b]], ob[b]);
     }
 }
 
@@ -268,7 +279,8 @@ __global__ void k_wall_setup(const double* __restrict__ xyz, const double* __res
 // solve computes bit-identical results alone and inside a batch.
 // ---------------------------------------------------------------------------
 struct View {
-  double *f, *fs, *g, *r, *rho, *mu, *lapr, *Fp;   // state and scratch
+  double *f, *fs, *g, *r, *rho, *mu, *lapr, *Fp;   // state and scratch; r is node-major:
+                                                   // [V][Q-1], pair p of node i at r + i(Q-1) + 2p
   double* drho;                                    // [D][V] reference gradient of rho (k_lap)
   int* flags;                                      // [0] setup, [1] non-finite
   const double *MJ, *Gm, *Me, *invMg, *Dm;        // geometry (MJ = M_e S J^-1), GLL D
@@ -549,12 +561,14 @@ __device__ __forceinline__ void body_rhs(const View& v, const double* __restrict
   const int le = tid / NL, k = tid - le * NL, lb = le * NL;
   const NodeIdx<D, NP> ix(k);
   const int64_t idx = base + tid;
-  double Dr[D][NP];
-  load_rows<D, NP>(sD, ix, false, Dr);
   double dr[D], dm[D];
 #pragma unroll
   for (int b = 0; b < D; ++b) dr[b] = v.drho[b * V + idx];
-  grad_ref<D, NP>(Dr, ix, smu + lb, k, dm);
+  {
+    double Dr[D][NP];
+    load_rows<D, NP>(sD, ix, false, Dr);
+    grad_ref<D, NP>(Dr, ix, smu + lb, k, dm);
+  }
   const double rh_node = sr[lb + k];
   const double rh3 = kInvCs2 * rh_node;
   double vv[D];   // d_b rho - (rho / c_s^2) d_b mu, reference components
@@ -577,7 +591,7 @@ __device__ __forceinline__ void body_rhs(const View& v, const double* __restrict
 #pragma unroll
     for (int b = 0; b < D; ++b) c[b] = L::template cdot<A>(J[b]);
     double dA[D], dB[D];
-    grad_ref2<D, NP>(Dr, ix, sg + (A - 1) * NT + lb, sg + (B - 1) * NT + lb, k, dA, dB);
+    grad_ref2<D, NP>(sD, ix, sg + (A - 1) * NT + lb, sg + (B - 1) * NT + lb, k, dA, dB);
     // r_A = M_e (t e_A.v - e_A.grad g_A), r_B = -M_e (t e_A.v - e_A.grad g_B), e_B = -e_A
     double cv = c[0] * vv[0];
 #pragma unroll
@@ -599,8 +613,8 @@ __device__ __forceinline__ void body_rhs(const View& v, const double* __restrict
         rB = fma(__ldg(v.wub + (int64_t)B * R + slot), rh_node, rB);
       }
     }
-    r[A * V + idx] = rA;
-    r[B * V + idx] = rB;
+    // node-major partials: the pair's two values side by side (one 16-byte store)
+    reinterpret_cast<double2*>(r + idx * (Q - 1))[decltype(RR)::value] = make_double2(rA, rB);
   });
 }
 
@@ -619,6 +633,17 @@ __device__ __forceinline__ double rk_update(int q, double sq, double imdt, doubl
   }
 }
 
+// copies of a global node whose local indices a gather-scatter thread loads up
+// front, so that the loads of all its copies are in flight together (a vertex
+// of a hex mesh has 8 copies); further copies are read in a loop
+constexpr int kCopiesAhead = 8;
+
+__device__ __forceinline__ void load_copies(const int* __restrict__ idx, int j0, int nc,
+                                            int (&ic)[kCopiesAhead]) {
+#pragma unroll
+  for (int c = 0; c < kCopiesAhead; ++c) ic[c] = (c < nc) ? idx[j0 + c] : 0;
+}
+
 // a5 (part 2): DSS of the right-hand side, M^-1, and the SSP-RK3 stage update
 //   stage 1: U1 = U0 + dt L;  stage 2: U2 = 3/4 U0 + 1/4 (U1 + dt L);
 //   stage 3: f^{n+1} = 1/3 U0 + 2/3 (U2 + dt L); rho of the new state
@@ -628,28 +653,58 @@ __device__ __forceinline__ double rk_update(int q, double sq, double imdt, doubl
 template <class L, int STAGE>
 __device__ __forceinline__ void body_dss_rk(const View& v, const double* gcur, double* out,
                                             int g) {
-  constexpr int Q = L::Q;
+  constexpr int Q = L::Q, NR = L::NREP;
   if (g >= v.G) return;
   const int64_t V = v.V;
   const int* __restrict__ off = v.off;
   const int* __restrict__ idx = v.idx;
-  const double* __restrict__ r = v.r;
+  const double2* __restrict__ r2 = reinterpret_cast<const double2*>(v.r);
   const double* __restrict__ U0 = v.fs;
   double* __restrict__ rho = v.rho;
   const int j0 = off[g], j1 = off[g + 1];
-  const int i0 = idx[j0];
+  const int nc = j1 - j0;
+  // the local indices of the first kCopiesAhead copies, in one round trip
+  int ic[kCopiesAhead];
+  load_copies(idx, j0, nc, ic);
+  const int i0 = ic[0];
   const double imdt = __ldg(v.invMg + g) * v.dt;   // dt L = dt DSS(r) / M_g
-  // DSS(r_q), summed copy by copy in the group's fixed order; the copy loop is
-  // outside the velocity loop so that each copy's Q-1 loads are independent
-  double val[Q];
-  val[0] = 0.0;   // the rest population does not stream
+  // DSS(r): the partials are node-major, pair p of a node at r2[node NR + p]
+  // (values of rep(p) and its opposite), summed copy by copy in the group's
+  // fixed order
+  double sa[NR], sb[NR];
 #pragma unroll
-  for (int q = 1; q < Q; ++q) val[q] = r[q * V + i0];
-  for (int j = j0 + 1; j < j1; ++j) {
+  for (int p = 0; p < NR; ++p) {
+    const double2 t = r2[(int64_t)i0 * NR + p];
+    sa[p] = t.x;
+    sb[p] = t.y;
+  }
+#pragma unroll
+  for (int c = 1; c < kCopiesAhead; ++c) {
+    if (c < nc) {
+#pragma unroll
+      for (int p = 0; p < NR; ++p) {
+        const double2 t = r2[(int64_t)ic[c] * NR + p];
+        sa[p] += t.x;
+        sb[p] += t.y;
+      }
+    }
+  }
+  for (int j = j0 + kCopiesAhead; j < j1; ++j) {
     const int ii = idx[j];
 #pragma unroll
-    for (int q = 1; q < Q; ++q) val[q] += r[q * V + ii];
+    for (int p = 0; p < NR; ++p) {
+      const double2 t = r2[(int64_t)ii * NR + p];
+      sa[p] += t.x;
+      sb[p] += t.y;
+    }
   }
+  double val[Q];
+  val[0] = 0.0;   // the rest population does not stream
+  static_for<0, NR>([&](auto P) {
+    constexpr int A = L::rep(decltype(P)::value), B = L::opp(A);
+    val[A] = sa[decltype(P)::value];
+    val[B] = sb[decltype(P)::value];
+  });
   double rs = 0.0;
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
@@ -657,7 +712,16 @@ __device__ __forceinline__ void body_dss_rk(const View& v, const double* gcur, d
     rs += val[q];
   }
   if (nonfinite(rs)) atomicOr(v.flags + 1, 1);
-  for (int j = j0; j < j1; ++j) {
+#pragma unroll
+  for (int c = 0; c < kCopiesAhead; ++c) {
+    if (c < nc) {
+      const int ii = ic[c];
+#pragma unroll
+      for (int q = 0; q < Q; ++q) out[q * V + ii] = val[q];
+      rho[ii] = rs;
+    }
+  }
+  for (int j = j0 + kCopiesAhead; j < j1; ++j) {
     const int ii = idx[j];
 #pragma unroll
     for (int q = 0; q < Q; ++q) out[q * V + ii] = val[q];
