@@ -168,6 +168,47 @@ def oracle_rate(case, steps, warmup=0):
     return case.nodes * steps / dt, dt, cores
 
 
+def _oracle_worker(job):
+    """One host core: the oracle on its own copy of the sample (spawned process)."""
+    name, steps = job
+    sys.path.insert(0, ROOT)
+    case, _ = sample_case(name)
+    rate, secs, _ = oracle_rate(case, steps, warmup=1)
+    return case.nodes * steps, secs
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def oracle_all_cores(name, steps):
+    """The oracle as it stands on every host core at once: one independent replica
+    of the bounded sample per core (spawned processes, one BLAS thread each);
+    throughput = the node-updates of all replicas / the slowest replica's time."""
+    import multiprocessing as mp
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
+    try:
+        with mp.get_context("spawn").Pool(cores) as pool:
+            res = pool.map(_oracle_worker, [(name, steps)] * cores)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    units = sum(u for u, _ in res)
+    return units / max(t for _, t in res), cores
+
+
 def reference_arm(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -244,47 +285,47 @@ def batched_section(args, device):
 
 
 def serving_section(args, device, capacity):
-    """Poisson stream of sweep requests through the continuous-batching server."""
+    """Poisson stream of relaxing requests through the continuous-batching server,
+    each run until KE_max < 1e-20 or its step budget: a quarter each of drops on
+    a flat wall, a cylinder and the sphere wall of Sec. 3.2, and periodic drops
+    (2D/3D); p50/p99 time to a converged answer and the aggregate rate."""
     from paper_2609_00535_b300 import serve
     n = args.serve_requests
-    probe = inputs.request_stream(n=n, rate=1.0, seed=5)
-    nodes = [r.E * (r.N + 1) ** (3 if "3d" in r.kind else 2) for r in probe]
-    work = sum(nodes) / len(nodes) * args.serve_max_steps
-    rate = 1.2 * capacity / work              # offered load 1.2x the measured capacity
-    reqs = inputs.request_stream(n=n, rate=rate, seed=5)
+    probe = inputs.relaxing_request_stream(n=n, rate=1.0, seed=8)
+    nodes = [r.case().nodes for r in probe]
+    work = sum(nodes) / len(nodes) * 0.5 * args.serve_max_steps
+    rate = 1.2 * capacity / work              # offered load ~1.2x the measured capacity
+    reqs = inputs.relaxing_request_stream(n=n, rate=rate, seed=8)
     srv = serve.Server(hbm_budget_bytes=int(args.serve_budget_gb * 2 ** 30),
                        epoch_steps=args.serve_epoch, ke_tol=1e-20,
                        max_steps=args.serve_max_steps, min_steps=args.serve_epoch)
     st = srv.run(reqs)
     out = st.summary()
-    out.update({"arrival_rate_per_s": rate, "offered_load": 1.2, "ke_tol": 1e-20,
+    conv = sorted(r.finished - r.arrival for r in st.records if r.converged)
+    by_kind = {}
+    for q, r in zip(sorted(reqs, key=lambda x: x.arrival), st.records):
+        e = by_kind.setdefault(q.kind, {"requests": 0, "converged": 0, "steps": [], "ke_capped": []})
+        e["requests"] += 1
+        if r.converged:
+            e["converged"] += 1
+            e["steps"].append(r.steps)
+        elif r.ke_max is not None:
+            e["ke_capped"].append(r.ke_max)
+    for e in by_kind.values():
+        st_ = sorted(e.pop("steps"))
+        ke = sorted(e.pop("ke_capped"))
+        e["median_steps_to_converge"] = st_[len(st_) // 2] if st_ else None
+        e["median_ke_when_capped"] = ke[len(ke) // 2] if ke else None
+    out.update({"workload": "relaxing requests: drops on a flat wall, a cylinder and a sphere "
+                            "wall, periodic drops 2D/3D; E %s, N 4; beta 0.1, force_split 1"
+                            % {k: list(v) for k, v in inputs.RELAX_SIZES.items()},
+                "by_kind": by_kind,
+                "converged_p50_s": conv[len(conv) // 2] if conv else None,
+                "converged_p99_s": conv[min(len(conv) - 1, int(round(0.99 * (len(conv) - 1))))]
+                if conv else None,
+                "arrival_rate_per_s": rate, "offered_load": 1.2, "ke_tol": 1e-20,
                 "max_steps": args.serve_max_steps, "epoch_steps": args.serve_epoch,
                 "hbm_budget_gb": args.serve_budget_gb})
-    return out
-
-
-def converging_serving_section(args, device):
-    """A stream of drop-radius sweep requests each run until KE_max < 1e-20."""
-    from paper_2609_00535_b300 import serve
-    reqs = inputs.converging_request_stream(n=args.converge_requests, rate=args.converge_rate,
-                                            seed=6)
-    srv = serve.Server(hbm_budget_bytes=int(args.serve_budget_gb * 2 ** 30), epoch_steps=500,
-                       ke_tol=1e-20, max_steps=60000, min_steps=1000)
-    st = srv.run(reqs)
-    out = st.summary()
-    steps = sorted(r.steps for r in st.records if r.finished is not None)
-    shapes = {}
-    for r in st.records:
-        key = r.name.rsplit("-", 1)[0]
-        e = shapes.setdefault(key, {"requests": 0, "converged": 0, "max_steps": 0})
-        e["requests"] += 1
-        e["converged"] += int(r.converged)
-        e["max_steps"] = max(e["max_steps"], r.steps)
-    out.update({"workload": "closed-box drops 2D, 6x6..9x9 elements at N 4, 6x6 at N 5, "
-                            "R 0.22-0.30, beta 0.1",
-                "by_shape": shapes,
-                "arrival_rate_per_s": args.converge_rate, "ke_tol": 1e-20, "max_steps": 60000,
-                "epoch_steps": 500, "median_steps_to_converge": steps[len(steps) // 2] if steps else None})
     return out
 
 
@@ -330,6 +371,47 @@ def angle_sweep_section(args, device):
     if both:
         out["steps_cap_over_disc"] = (sum(steps_by["cap"][q] for q in both)
                                       / sum(steps_by["disc"][q] for q in both))
+    return out
+
+
+def config_lines_section(args, device):
+    """Plain single-solve lines of the two 2D workloads: the flat-wall droplet
+    (8x8 quads, N = 4, 1,600 nodes) and the droplet on a cylinder (1,024 curved
+    quads, N = 6, 50,176 nodes); node-updates/s and the k_rhs FP64 roofline."""
+    import torch
+    from paper_2609_00535_b300 import semlbm
+    peak, _ = semlbm.fp64_peak_tflops(device)
+    out = {}
+    for name in ("flat2d", "cylinder2d"):
+        case = make_case(name)
+        s = semlbm.Solver.from_case(case, device=device)
+        s.set_density(case.rho0)
+        s.step(5)
+        s.synchronize()
+        K = args.config_steps
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s.stream)
+        s.step(K)                            # graph replay, as a user runs it
+        e1.record(s.stream)
+        s.synchronize()
+        ms = e0.elapsed_time(e1)
+        s.profile(True)                      # per-kernel events on a second run
+        s.step(K)
+        prof = s.profile_read()
+        s.profile(False)
+        info = s.info
+        rhs_ms = prof["ms"]["k_rhs"] / max(prof["launches"]["k_rhs"], 1)
+        work = flopcount.rhs_work(case.lattice, case.mesh.N, info["n_local"], info["n_wall_nodes"])
+        ach = work["flops"] / (rhs_ms * 1e-3) / 1e12
+        out[name] = {"mesh": "%d quads, N=%d" % (case.mesh.n_elem, case.mesh.N),
+                     "nodes": info["n_local"], "steps": K,
+                     "node_updates_per_s": info["n_local"] * K / (ms * 1e-3),
+                     "ms_per_step": ms / K, "us_per_step": 1e3 * ms / K,
+                     "k_rhs_ms": rhs_ms, "k_rhs_tflops": ach, "k_rhs_frac": ach / peak,
+                     "k_rhs_pair_groups": info["rhs_pair_groups"],
+                     "status": s.diagnostics()["status"]}
+        s.close()
     return out
 
 
@@ -465,22 +547,30 @@ def native_arm(args):
 
     line = None
     if rank == 0:
-        cpu = None
+        cpu = cpu1 = None
         if not args.no_cpu_baseline:
             cpu_steps = args.cpu_steps
             rate, secs, cores = oracle_rate(case, cpu_steps)
-            cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-                   "sample": "%d time steps of the full %s mesh (%d nodes), %.1f s" %
-                             (cpu_steps, args.config, case.nodes, secs)}
+            cpu1 = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                    "sample": "%d time steps of the full %s mesh (%d nodes), %.1f s" %
+                              (cpu_steps, args.config, case.nodes, secs),
+                    "cpu": cpu_model()}
+            scase, what = sample_case(args.config)
+            rate_all, ncores = oracle_all_cores(args.config, args.cpu_sample_steps)
+            cpu = {"value": rate_all, "unit": UNIT, "cores": ncores, "kind": "oracle",
+                   "sample": "one replica per core of %d time steps of %s" %
+                             (args.cpu_sample_steps, what),
+                   "nproc": os.cpu_count(), "cpu": cpu_model(),
+                   "single_core_full_mesh": rate}
         batched = serving = None
         if not args.no_batched:
             batched = batched_section(args, device)
         lattices = None if args.no_lattices else lattice_section(args, device)
-        serving_converge = sweep = None
+        configs = None if args.no_configs else config_lines_section(args, device)
+        sweep = None
         if not args.no_serving:
             cap = batched["batched_node_updates_per_s"] if batched else value
             serving = serving_section(args, device, cap)
-            serving_converge = converging_serving_section(args, device)
             sweep = angle_sweep_section(args, device)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -516,9 +606,10 @@ def native_arm(args):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": Q * V * 8,
                     "d2h_bytes_per_step": 80, "steps": e2e_steps},
             "cpu_baseline": cpu,
+            "cpu_baseline_1core": cpu1,
+            "configs": configs,
             "batched": batched,
             "serving": serving,
-            "serving_to_convergence": serving_converge,
             "angle_sweep": sweep,
             "lattices": lattices,
             "final_diag": {"ke_max": d["ke_max"], "mass": d["mass"], "status": d["status"]},
@@ -542,14 +633,17 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--batch-solves", type=int, default=64)
-    ap.add_argument("--batch-steps", type=int, default=20)
+    ap.add_argument("--batch-steps", type=int, default=2000)
+    ap.add_argument("--config-steps", type=int, default=200,
+                    help="steps of the flat-wall and cylinder plain lines")
+    ap.add_argument("--no-configs", action="store_true", help="skip the 2D plain lines")
+    ap.add_argument("--cpu-sample-steps", type=int, default=60,
+                    help="oracle steps per core replica of the bounded sample")
     ap.add_argument("--serve-requests", type=int, default=100)
-    ap.add_argument("--serve-max-steps", type=int, default=300)
-    ap.add_argument("--serve-epoch", type=int, default=50)
+    ap.add_argument("--serve-max-steps", type=int, default=100000)
+    ap.add_argument("--serve-epoch", type=int, default=500)
     ap.add_argument("--serve-budget-gb", type=float, default=40.0)
-    ap.add_argument("--converge-requests", type=int, default=100)
-    ap.add_argument("--converge-rate", type=float, default=20.0)
-    ap.add_argument("--sweep-requests", type=int, default=32)
+    ap.add_argument("--sweep-requests", type=int, default=16)
     ap.add_argument("--lattice-steps", type=int, default=50)
     ap.add_argument("--no-lattices", action="store_true", help="skip the D3Q19/D3Q27 lines")
     ap.add_argument("--sweep-max-steps", type=int, default=100000)

@@ -414,10 +414,94 @@ def mixed_case(rng, kind, E, N, theta, radius_scale=1.0):
                            R=0.25 * radius_scale, init="cap" if kind == "capwall2d" else "disc")
     elif kind == "boxdrop2d":
         c = closed_box_drop(N=N, ne=max(4, int(round(math.sqrt(E)))), R=0.25 * radius_scale)
+    elif kind.startswith("relax"):
+        c = relaxing_case(kind, E, N, theta, radius_scale)
     else:
         raise ValueError(kind)
     c.name = "%s-E%d-N%d-%.0fdeg" % (kind, c.mesh.n_elem, N, math.degrees(theta))
     return c
+
+
+def viscous_tau(dt, L, steps=1.0e4):
+    """Relaxation time that makes the viscous time L^2 / nu of a domain of size L
+    last about `steps` time steps (nu = tau c_s^2 dt), and at least 1."""
+    return max(1.0, L * L / ((1.0 / 3.0) * dt * dt * steps))
+
+
+def relaxing_case(kind, E, N, theta, radius_scale=1.0, beta=0.1, rho_l=1.0, rho_v=0.1, cfl=0.4):
+    """Requests that relax to rest (the serving stream run to a kinetic-energy
+    threshold): stiff surface tension (beta = 0.1), interface width 3 node
+    spacings (2.5 on the 3D sphere wall), tau from viscous_tau so the slowest
+    viscous mode decays within ~1e4 steps, each drop started at its equilibrium
+    cap, and the potential-part force reading in F** (force_split = 1, under
+    which a drop at rest is linearly stable; with the printed force a periodic
+    drop at rest has a growing mode).  Kinds:
+      relaxflat2d    cap on the wall y = 0 of [0, 2] x [0, 1], 2 ne x ne quads
+      relaxcyl2d     cap on a cylinder of radius 0.15 (curved O-grid, rotated frames)
+      relaxsphere3d  cap on the sphere wall of the Sec. 3.2 box (ne^3 curved hexes)
+      relaxdrop2d / relaxdrop3d   drop of diameter 0.5 in a periodic unit box
+    E sets the element count (rounded to each generator's grid)."""
+    if kind == "relaxflat2d":
+        ne = max(3, int(round(math.sqrt(E / 2.0))))
+        mesh = box((2 * ne, ne), (0.0, 0.0), (2.0, 1.0), N, face_tags={2: 0})
+        h = 1.0 / (ne * N)
+        delta, L, lat = 3 * h, 1.0, "D2Q9"
+        rho0 = sessile_cap_density(mesh, 1.0, 0.5 * math.pi * (0.25 * radius_scale) ** 2, theta,
+                                   delta, rho_l, rho_v)
+    elif kind == "relaxcyl2d":
+        Rc = 0.15
+        n_r = max(3, int(round(math.sqrt(E / 6.0))))
+        n_t = max(12, int(round(E / n_r)))
+        mesh = rotate_elements(cylinder_ogrid(N, n_theta=n_t, n_r=n_r, Rc=Rc), 2)
+        delta, L, lat = 3 * 2 * math.pi * Rc / n_t / N, 0.5 - Rc, "D2Q9"
+        rho0 = cylinder_cap_density(mesh, (0.5, 0.5), Rc, 0.15 * radius_scale, theta, delta,
+                                    rho_l, rho_v)
+    elif kind == "relaxsphere3d":
+        ne = max(3, int(round(E ** (1.0 / 3.0))))
+        mesh = sphere_cap_box(N, (ne, ne, ne))
+        delta, L, lat = 2.5 * 0.5 / (ne * N), 0.5, "D3Q13"
+        rho0 = curved_cap_density(mesh, (0.25, 0.25, -0.7), 0.7, 0.13 * radius_scale, theta,
+                                  delta, (0.0, 0.0, 1.0), rho_l, rho_v)
+    elif kind in ("relaxdrop2d", "relaxdrop3d"):
+        dim = 2 if kind == "relaxdrop2d" else 3
+        ne = max(2, int(round(E ** (1.0 / dim))))
+        mesh = box((ne,) * dim, (0.0,) * dim, (1.0,) * dim, N, periodic=(True,) * dim)
+        delta, L, lat = 3.0 / (ne * N), 1.0, "D2Q9" if dim == 2 else "D3Q13"
+        rho0 = droplet_density(mesh, (0.5,) * dim, 0.25 * radius_scale, delta, rho_l, rho_v)
+        theta = math.pi / 2
+    else:
+        raise ValueError(kind)
+    kappa = kappa_from_width(beta, delta, rho_l, rho_v)
+    dt = cfl_dt(mesh, lat, cfl, kappa, rho_l)
+    return Case(kind, mesh, lat, rho_l, rho_v, beta, kappa, viscous_tau(dt, L), dt, theta, (),
+                rho0, 0, {"delta": delta}, force_split=1)
+
+
+# element-count ranges of the relaxing request kinds (sizes whose slowest modes
+# decay to KE_max < 1e-20 within a few 1e4 steps where the physics allows it)
+RELAX_SIZES = {"relaxflat2d": (32, 72), "relaxcyl2d": (72, 150), "relaxsphere3d": (27, 64),
+               "relaxdrop2d": (16, 64), "relaxdrop3d": (27, 125)}
+
+
+def relaxing_request_stream(n=500, rate=10.0, seed=8, orders=(4,)):
+    """Poisson stream run to a kinetic-energy threshold: a quarter each of drops
+    on a flat wall, on a cylinder and on the sphere wall of Sec. 3.2, and
+    isolated periodic drops (2D or 3D); E log-uniform in each kind's range
+    (RELAX_SIZES), N uniform in `orders`, contact angle uniform in [15, 165]
+    degrees, drop size x [0.9, 1.1]."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    kinds = ["relaxflat2d", "relaxcyl2d", "relaxsphere3d", "relaxdrop"]
+    out = []
+    for i in range(n):
+        t += rng.exponential(1.0 / rate)
+        kind = kinds[i % 4]
+        if kind == "relaxdrop":
+            kind = "relaxdrop2d" if rng.random() < 0.5 else "relaxdrop3d"
+        out.append(Request(i, t, kind, _log_uniform_int(rng, *RELAX_SIZES[kind]),
+                           int(rng.choice(orders)), math.radians(rng.uniform(15.0, 165.0)),
+                           float(rng.uniform(0.9, 1.1)), int(rng.integers(1 << 30))))
+    return out
 
 
 def cap_on_wall_2d(theta, N=4, ne=8, R=0.25, beta=0.1, delta=0.1, tau=1.0, rho_l=1.0,

@@ -130,3 +130,25 @@ def test_generator_defaults_match_the_paper():
     wall = s.mesh.node_xyz[s.mesh.face_kind[:, 4] == 1][:, :n * n].reshape(-1, 3)   # l = 0 face nodes
     r = np.linalg.norm(wall - [0.25, 0.25, -sph["sphere_D"] / 2], axis=1)
     assert len(wall) > 0 and np.allclose(r, sph["sphere_D"] / 2, atol=1e-12)
+
+
+def test_relaxing_request_stream():
+    """The serving stream run to a KE threshold: a quarter each of flat-wall,
+    cylinder and sphere-wall caps and periodic drops, sizes in each kind's
+    range, the potential-part force reading, and tau from the viscous-time rule."""
+    reqs = inputs.relaxing_request_stream(n=40, rate=10.0, seed=8)
+    assert all(b.arrival > a.arrival for a, b in zip(reqs, reqs[1:]))
+    kinds = [r.kind for r in reqs]
+    assert kinds.count("relaxflat2d") == kinds.count("relaxcyl2d") == kinds.count("relaxsphere3d") == 10
+    assert kinds.count("relaxdrop2d") + kinds.count("relaxdrop3d") == 10
+    for r in reqs[:8]:
+        lo, hi = inputs.RELAX_SIZES[r.kind]
+        assert lo <= r.E <= hi
+        c = r.case()
+        assert c.force_split == 1 and c.beta == 0.1 and c.tau >= 1.0
+        assert c.lattice == ("D3Q13" if r.kind.endswith("3d") else "D2Q9")
+        assert c.tau == pytest.approx(max(1.0, inputs.viscous_tau(c.dt, 1.0 if "flat" in r.kind or "drop" in r.kind
+                                                                  else (0.35 if "cyl" in r.kind else 0.5))))
+        assert c.rho0.max() > 0.85 and abs(c.rho0.min() - c.rho_v) < 2e-3   # a drop in vapour
+    assert inputs.viscous_tau(0.01, 1.0, steps=1e4) == pytest.approx(3.0)
+    assert inputs.viscous_tau(0.1, 1.0) == 1.0
