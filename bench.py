@@ -230,12 +230,31 @@ def reference_arm(args):
     return 0
 
 
-def batched_section(args, device):
+def small_solves(n=64, seed=9):
+    """The paper's own problem sizes: the flat-wall drop (8x8 quads, N = 4, 1,600
+    nodes) at angles uniform in 15-165 degrees and the isolated periodic drop of
+    Sec. 3.3 (4x4 quads, N = 8, 1,296 nodes, force_split 1), half and half."""
+    import math
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        if i % 2 == 0:
+            out.append(inputs.flat_wall_2d(theta=math.radians(rng.uniform(15.0, 165.0))))
+        else:
+            c = inputs.periodic_droplet(dim=2, ne=4, N=8, D=0.5 * rng.uniform(0.9, 1.1))
+            c.force_split = 1
+            out.append(c)
+    return out
+
+
+def batched_section(args, device, cases=None):
     """64 solves of uneven E, N and angle: 64 sequential plain solves against one
     autotuned batch (every solve advances the same number of steps in both)."""
     import torch
     from paper_2609_00535_b300 import semlbm
-    cases = inputs.batch_mix(n=args.batch_solves, seed=4)
+    if cases is None:
+        cases = inputs.batch_mix(n=args.batch_solves, seed=4)
     solvers = []
     for c in cases:
         s = semlbm.Solver.from_case(c, device=device)
@@ -415,6 +434,58 @@ def config_lines_section(args, device):
     return out
 
 
+def angle_resolution_section(args, device):
+    """Static contact angle on a flat wall against the interface width: the drop
+    of the angle sweep (area of a half-disc of radius R = 0.25 on the wall y = 0 of
+    [0, 2] x [0, 1], beta 0.1, tau 1, started at its equilibrium cap) at
+    delta / R = 0.4, 0.2 and 0.1 with delta = 3.2 node spacings (16x8, 32x16 and
+    64x32 quads at N = 4), and at delta / R = 0.4 with N = 8 (the same width over
+    twice the nodes).  Each solve runs in one batch until KE_max < 1e-14 or its
+    step budget; the angle comes from the device wetting moments with the
+    diffuse-interface correction (wetting.contact_angle)."""
+    import math
+    from paper_2609_00535_b300 import semlbm, wetting
+    meshes = [(8, 4, 0.1), (16, 4, 0.05), (32, 4, 0.025), (8, 8, 0.1)]
+    angles = [float(a) for a in args.angle_study_degrees.split(",")]
+    b = semlbm.Batch(device=device)
+    live = {}
+    for ne, N, delta in meshes:
+        for deg in angles:
+            c = inputs.cap_on_wall_2d(math.radians(deg), N=N, ne=ne, delta=delta)
+            c.force_split = 1
+            s = semlbm.Solver.from_case(c, device=device)
+            s.set_density(c.rho0)
+            live[b.add(s)] = (ne, N, delta, deg, s)
+    out = []
+    done = 0
+    while live and done < args.angle_study_max_steps:
+        b.step(args.angle_study_epoch)
+        done += args.angle_study_epoch
+        diag = b.diagnostics()
+        for slot in list(live):
+            ne, N, delta, deg, s = live[slot]
+            d = diag[slot]
+            if d["status"] == 0 and d["ke_max"] >= 1e-14 and done < args.angle_study_max_steps:
+                continue
+            b.remove(slot)
+            row = {"mesh": "%dx%d quads, N=%d" % (2 * ne, ne, N), "delta_over_R": delta / 0.25,
+                   "theta_deg": deg, "steps": done, "ke_max": d["ke_max"], "status": d["status"]}
+            row["rho_min"], row["rho_max"] = d["rho_min"], d["rho_max"]
+            if d["status"] == 0:
+                m = s.wetting_moments(0)
+                row["volume"], row["wetted"] = m["volume"], m["wetted"]
+                try:
+                    row["measured_deg"] = wetting.contact_angle(m, 2, delta=delta)
+                    row["error_deg"] = row["measured_deg"] - deg
+                except ValueError as exc:       # no drop left on the wall
+                    row["error"] = str(exc)
+            out.append(row)
+            s.close()
+            del live[slot]
+    b.close()
+    return out
+
+
 def lattice_section(args, device):
     """The sphere workload with the cubic velocity sets D3Q19 and D3Q27 (same mesh,
     N and parameters): node-updates/s and the k_rhs FP64 roofline of each."""
@@ -562,10 +633,12 @@ def native_arm(args):
                              (args.cpu_sample_steps, what),
                    "nproc": os.cpu_count(), "cpu": cpu_model(),
                    "single_core_full_mesh": rate}
-        batched = serving = None
+        batched = batched_small = serving = None
         if not args.no_batched:
             batched = batched_section(args, device)
+            batched_small = batched_section(args, device, small_solves())
         lattices = None if args.no_lattices else lattice_section(args, device)
+        angle_study = angle_resolution_section(args, device) if args.angle_study else None
         configs = None if args.no_configs else config_lines_section(args, device)
         sweep = None
         if not args.no_serving:
@@ -609,9 +682,11 @@ def native_arm(args):
             "cpu_baseline_1core": cpu1,
             "configs": configs,
             "batched": batched,
+            "batched_small": batched_small,
             "serving": serving,
             "angle_sweep": sweep,
             "lattices": lattices,
+            "angle_resolution": angle_study,
             "final_diag": {"ke_max": d["ke_max"], "mass": d["mass"], "status": d["status"]},
         }
         print(json.dumps(line), flush=True)
@@ -645,6 +720,11 @@ def main():
     ap.add_argument("--serve-budget-gb", type=float, default=40.0)
     ap.add_argument("--sweep-requests", type=int, default=16)
     ap.add_argument("--lattice-steps", type=int, default=50)
+    ap.add_argument("--angle-study", action="store_true",
+                    help="flat-wall contact angle at three interface widths (minutes)")
+    ap.add_argument("--angle-study-degrees", default="60,90,120")
+    ap.add_argument("--angle-study-epoch", type=int, default=2000)
+    ap.add_argument("--angle-study-max-steps", type=int, default=600000)
     ap.add_argument("--no-lattices", action="store_true", help="skip the D3Q19/D3Q27 lines")
     ap.add_argument("--sweep-max-steps", type=int, default=100000)
     ap.add_argument("--ne", type=int, default=None,

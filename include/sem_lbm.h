@@ -141,6 +141,10 @@ typedef struct {
                                 batch in the streaming right-hand side: 1 = one
                                 CTA per element batch (meshes that fill the GPU),
                                 > 1 = the pair-split form for small meshes      */
+  int graph_pdl;             /* 1 once the captured step launches each kernel after
+                                the first as a programmatic dependent of the one
+                                before (its launch overlaps the predecessor's end;
+                                its data accesses still follow it), 0 otherwise  */
 } sem_lbm_info_t;
 
 /* Device bytes sem_lbm_create needs for this mesh (for admission control and

@@ -44,28 +44,31 @@ struct GroupOps {
   int epb = 0, threads = 0;
   size_t sm_lap = 0, sm_force = 0, sm_rhs = 0;
   int grid_lap = 0, grid_force = 0, grid_rhs = 0, grid_node = 0;
-  void (*step)(const GroupOps&, const GroupDev&, cudaStream_t) = nullptr;
+  void (*step)(const GroupOps&, const GroupDev&, cudaStream_t, bool pdl) = nullptr;
 };
 
 template <class L, int NP, int EPB>
-void group_step(const GroupOps& o, const GroupDev& d, cudaStream_t st) {
+void group_step(const GroupOps& o, const GroupDev& d, cudaStream_t st, bool pdl) {
   constexpr int T = cta_threads<L::D, NP, EPB>();
   const int* ce = d.counts;
   const int* cn = d.counts + 1;
-  kb_lap<L, NP, EPB><<<o.grid_lap, T, o.sm_lap, st>>>(d.views, d.elem, ce);
-  kb_dss_mu<L><<<o.grid_node, kDssThreads, 0, st>>>(d.views, d.node, cn);
-  kb_force<L, NP, EPB><<<o.grid_force, T, o.sm_force, st>>>(d.views, d.elem, ce);
-  kb_dss_collide<L><<<o.grid_node, kDssThreads, 0, st>>>(d.views, d.node, cn);
-  kb_rhs<L, NP, EPB><<<o.grid_rhs, T, o.sm_rhs, st>>>(d.views, d.elem, ce, 1);
-  kb_dss_rk<L, 1><<<o.grid_node, kDssThreads, 0, st>>>(d.views, d.node, cn);
-  kb_lap<L, NP, EPB><<<o.grid_lap, T, o.sm_lap, st>>>(d.views, d.elem, ce);
-  kb_dss_mu<L><<<o.grid_node, kDssThreads, 0, st>>>(d.views, d.node, cn);
-  kb_rhs<L, NP, EPB><<<o.grid_rhs, T, o.sm_rhs, st>>>(d.views, d.elem, ce, 0);
-  kb_dss_rk<L, 2><<<o.grid_node, kDssThreads, 0, st>>>(d.views, d.node, cn);
-  kb_lap<L, NP, EPB><<<o.grid_lap, T, o.sm_lap, st>>>(d.views, d.elem, ce);
-  kb_dss_mu<L><<<o.grid_node, kDssThreads, 0, st>>>(d.views, d.node, cn);
-  kb_rhs<L, NP, EPB><<<o.grid_rhs, T, o.sm_rhs, st>>>(d.views, d.elem, ce, 0);
-  kb_dss_rk<L, 3><<<o.grid_node, kDssThreads, 0, st>>>(d.views, d.node, cn);
+  // with pdl, every kernel after the first is a programmatic dependent launch
+  // of the one before it on the group's stream
+  launch(kb_lap<L, NP, EPB>, o.grid_lap, T, o.sm_lap, st, false, d.views, d.elem, ce);
+  launch(kb_dss_mu<L>, o.grid_node, kDssThreads, 0, st, pdl, d.views, d.node, cn);
+  launch(kb_force<L, NP, EPB>, o.grid_force, T, o.sm_force, st, pdl, d.views, d.elem, ce);
+  launch(kb_dss_collide<L>, o.grid_node, kDssThreads, 0, st, pdl, d.views, d.node, cn);
+  launch(kb_rhs<L, NP, EPB>, o.grid_rhs, T, o.sm_rhs, st, pdl, d.views, d.elem, ce, 1);
+  launch(kb_dss_rk<L, 1>, o.grid_node, kDssThreads, 0, st, pdl, d.views, d.node, cn);
+  for (int stage = 2; stage <= 3; ++stage) {
+    launch(kb_lap<L, NP, EPB>, o.grid_lap, T, o.sm_lap, st, pdl, d.views, d.elem, ce);
+    launch(kb_dss_mu<L>, o.grid_node, kDssThreads, 0, st, pdl, d.views, d.node, cn);
+    launch(kb_rhs<L, NP, EPB>, o.grid_rhs, T, o.sm_rhs, st, pdl, d.views, d.elem, ce, 0);
+    if (stage == 2)
+      launch(kb_dss_rk<L, 2>, o.grid_node, kDssThreads, 0, st, pdl, d.views, d.node, cn);
+    else
+      launch(kb_dss_rk<L, 3>, o.grid_node, kDssThreads, 0, st, pdl, d.views, d.node, cn);
+  }
 }
 
 template <class K>
@@ -253,7 +256,7 @@ int refresh_group(sem_lbm_batch* b, BatchGroup* g) {
 
 GroupDev dev_of(const BatchGroup* g) { return GroupDev{g->d_views, g->d_elem, g->d_node, g->d_counts}; }
 
-int capture(sem_lbm_batch* b) {
+int capture(sem_lbm_batch* b, bool pdl) {
   if (b->graph) {
     cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
@@ -265,7 +268,7 @@ int capture(sem_lbm_batch* b) {
   cudaError_t e = cudaEventRecord(b->fork, b->stream);
   for (BatchGroup* g : b->groups) {
     if (e == cudaSuccess) e = cudaStreamWaitEvent(g->branch, b->fork, 0);
-    if (e == cudaSuccess) g->cands[g->choice].step(g->cands[g->choice], dev_of(g), g->branch);
+    if (e == cudaSuccess) g->cands[g->choice].step(g->cands[g->choice], dev_of(g), g->branch, pdl);
     if (e == cudaSuccess) e = cudaEventRecord(g->join, g->branch);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, g->join, 0);
   }
@@ -407,13 +410,20 @@ int sem_lbm_batch_step(sem_lbm_batch_t* b, int64_t n_steps) {
   if (n_steps < 0) return fail(SEMLBM_EINVAL, "n_steps must be >= 0");
   if (b->groups.empty() || n_steps == 0) return 0;
   if (b->dirty || !b->graph) {
-    if (capture(b) != 0) {
+    // programmatic edges between each group's kernels first, else plain edges
+    int rc = capture(b, true);
+    if (rc != 0) {
+      cudaGetLastError();
+      rc = capture(b, false);
+    }
+    if (rc != 0) {
       // a capture that failed leaves no graph: run these steps as direct
       // launches of the same kernels (same results) and capture next time
       cudaGetLastError();
       ++b->capture_failures;
       for (int64_t i = 0; i < n_steps; ++i)
-        for (BatchGroup* g : b->groups) g->cands[g->choice].step(g->cands[g->choice], dev_of(g), b->stream);
+        for (BatchGroup* g : b->groups)
+          g->cands[g->choice].step(g->cands[g->choice], dev_of(g), b->stream, false);
       CUDA_TRY(cudaGetLastError());
       for (sem_lbm* s : b->slots)
         if (s) s->step += n_steps;
@@ -443,7 +453,7 @@ int sem_lbm_batch_tune(sem_lbm_batch_t* b, int steps_per_candidate) {
       const GroupOps& o = g->cands[c];
       // a warm-up step, drained before timing (first launches can load modules
       // and stall), then the best of two timed runs of steps_per_candidate - 1
-      o.step(o, dev_of(g), b->stream);
+      o.step(o, dev_of(g), b->stream, false);
       if (cudaStreamSynchronize(b->stream) != cudaSuccess) {
         rc = fail(SEMLBM_ECUDA, "tuning step failed: %s", cudaGetErrorString(cudaGetLastError()));
         break;
@@ -451,7 +461,7 @@ int sem_lbm_batch_tune(sem_lbm_batch_t* b, int steps_per_candidate) {
       double per = 1e300;
       for (int rep = 0; rep < 2 && rc == 0; ++rep) {
         cudaEventRecord(e0, b->stream);
-        for (int k = 1; k < steps_per_candidate; ++k) o.step(o, dev_of(g), b->stream);
+        for (int k = 1; k < steps_per_candidate; ++k) o.step(o, dev_of(g), b->stream, false);
         cudaEventRecord(e1, b->stream);
         if (cudaEventSynchronize(e1) != cudaSuccess) {
           rc = fail(SEMLBM_ECUDA, "tuning step failed: %s", cudaGetErrorString(cudaGetLastError()));

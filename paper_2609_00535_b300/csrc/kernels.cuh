@@ -106,6 +106,20 @@ __device__ __forceinline__ void stage_in(double* __restrict__ s, const double* _
   for (int i = threadIdx.x; i < count; i += blockDim.x) s[i] = __ldg(g + base + i);
 }
 
+// Programmatic dependent launch (sm_90 and later): a kernel launched with the
+// programmatic-serialization attribute may start while its predecessor on the
+// stream is still running; pdl_wait() blocks until the predecessor has
+// completed and its memory is visible, and is a no-op for an ordinary launch.
+// pdl_trigger() lets the successor be scheduled once every CTA of this kernel
+// has issued it (or exited).  The step kernels wait before touching global
+// memory, so every data dependency is that of a serialised stream, and trigger
+// after their work: a successor triggered at the start would occupy SM slots
+// with waiting CTAs for the whole of its predecessor (and, transitively, pull
+// the rest of the step in behind it), which slowed concurrent branches of a
+// batch and split-pair meshes by up to 45 %.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ bool nonfinite(double x) {
   return ((__double_as_longlong(x) >> 52) & 0x7ff) == 0x7ff;
 }
@@ -745,23 +759,31 @@ __global__ void __launch_bounds__(cta_threads<L::D, NP, EPB>())
     k_lap(View v, const double* __restrict__ rho, double* __restrict__ out,
           double* __restrict__ drho) {
   extern __shared__ double sm[];
+  pdl_wait();
   body_lap<L, NP, EPB>(v, rho, out, drho, blockIdx.x, sm);
+  pdl_trigger();
 }
 
 static __global__ void k_dss_mu(View v, const double* __restrict__ lapr, const double* __restrict__ rho,
                          double* __restrict__ mu) {
+  pdl_wait();
   body_dss_mu(v, lapr, rho, mu, blockIdx.x * blockDim.x + threadIdx.x);
+  pdl_trigger();
 }
 
 template <class L, int NP, int EPB>
 __global__ void __launch_bounds__(cta_threads<L::D, NP, EPB>()) k_force(View v) {
   extern __shared__ double sm[];
+  pdl_wait();
   body_force<L, NP, EPB>(v, blockIdx.x, sm);
+  pdl_trigger();
 }
 
 template <class L>
 __global__ void k_dss_collide(View v) {
+  pdl_wait();
   body_dss_collide<L>(v, blockIdx.x * blockDim.x + threadIdx.x);
+  pdl_trigger();
 }
 
 template <class L, int NP, int EPB, bool SPLIT>
@@ -770,17 +792,21 @@ __global__ void __launch_bounds__(cta_threads<L::D, NP, EPB>(), rhs_min_blocks<L
   // SPLIT: the velocity pairs of each element batch are spread over gridDim.y
   // CTAs (meshes too small to fill the GPU with one CTA per element batch)
   extern __shared__ double sm[];
+  pdl_wait();
   if constexpr (SPLIT) {
     const int P = gridDim.y, y = blockIdx.y;
     body_rhs<L, NP, EPB, true>(v, gst, blockIdx.x, sm, y * L::NREP / P, (y + 1) * L::NREP / P);
   } else {
     body_rhs<L, NP, EPB>(v, gst, blockIdx.x, sm);
   }
+  pdl_trigger();
 }
 
 template <class L, int STAGE>
 __global__ void k_dss_rk(View v, const double* gcur, double* out) {
+  pdl_wait();
   body_dss_rk<L, STAGE>(v, gcur, out, blockIdx.x * blockDim.x + threadIdx.x);
+  pdl_trigger();
 }
 
 // ---------------------------------------------------------------------------
@@ -798,6 +824,7 @@ __global__ void __launch_bounds__(cta_threads<L::D, NP, EPB>())
     kb_lap(const View* __restrict__ slots, const WorkItem* __restrict__ items,
            const int* __restrict__ count) {
   extern __shared__ double sm[];
+  pdl_wait();
   const int n = *count;
   for (int w = blockIdx.x; w < n; w += gridDim.x) {
     const WorkItem it = items[w];
@@ -805,17 +832,20 @@ __global__ void __launch_bounds__(cta_threads<L::D, NP, EPB>())
     body_lap<L, NP, EPB>(v, v.rho, v.lapr, v.drho, it.unit, sm);
     __syncthreads();
   }
+  pdl_trigger();
 }
 
 template <class L>
 __global__ void kb_dss_mu(const View* __restrict__ slots, const WorkItem* __restrict__ items,
                           const int* __restrict__ count) {
+  pdl_wait();
   const int n = *count;
   for (int w = blockIdx.x; w < n; w += gridDim.x) {
     const WorkItem it = items[w];
     const View& v = slots[it.slot];
     body_dss_mu(v, v.lapr, v.rho, v.mu, it.unit * blockDim.x + threadIdx.x);
   }
+  pdl_trigger();
 }
 
 template <class L, int NP, int EPB>
@@ -823,22 +853,26 @@ __global__ void __launch_bounds__(cta_threads<L::D, NP, EPB>())
     kb_force(const View* __restrict__ slots, const WorkItem* __restrict__ items,
              const int* __restrict__ count) {
   extern __shared__ double sm[];
+  pdl_wait();
   const int n = *count;
   for (int w = blockIdx.x; w < n; w += gridDim.x) {
     const WorkItem it = items[w];
     body_force<L, NP, EPB>(slots[it.slot], it.unit, sm);
     __syncthreads();
   }
+  pdl_trigger();
 }
 
 template <class L>
 __global__ void kb_dss_collide(const View* __restrict__ slots, const WorkItem* __restrict__ items,
                                const int* __restrict__ count) {
+  pdl_wait();
   const int n = *count;
   for (int w = blockIdx.x; w < n; w += gridDim.x) {
     const WorkItem it = items[w];
     body_dss_collide<L>(slots[it.slot], it.unit * blockDim.x + threadIdx.x);
   }
+  pdl_trigger();
 }
 
 template <class L, int NP, int EPB>
@@ -846,6 +880,7 @@ __global__ void __launch_bounds__(cta_threads<L::D, NP, EPB>(), rhs_min_blocks<L
     kb_rhs(const View* __restrict__ slots, const WorkItem* __restrict__ items,
            const int* __restrict__ count, int from_fs) {
   extern __shared__ double sm[];
+  pdl_wait();
   const int n = *count;
   for (int w = blockIdx.x; w < n; w += gridDim.x) {
     const WorkItem it = items[w];
@@ -853,11 +888,13 @@ __global__ void __launch_bounds__(cta_threads<L::D, NP, EPB>(), rhs_min_blocks<L
     body_rhs<L, NP, EPB>(v, from_fs ? v.fs : v.g, it.unit, sm);
     __syncthreads();
   }
+  pdl_trigger();
 }
 
 template <class L, int STAGE>
 __global__ void kb_dss_rk(const View* __restrict__ slots, const WorkItem* __restrict__ items,
                           const int* __restrict__ count) {
+  pdl_wait();
   const int n = *count;
   for (int w = blockIdx.x; w < n; w += gridDim.x) {
     const WorkItem it = items[w];
@@ -866,6 +903,7 @@ __global__ void kb_dss_rk(const View* __restrict__ slots, const WorkItem* __rest
     double* out = (STAGE == 3) ? v.f : v.g;
     body_dss_rk<L, STAGE>(v, gcur, out, it.unit * blockDim.x + threadIdx.x);
   }
+  pdl_trigger();
 }
 
 // a6: diagnostics (Sec. 3.3 KE_max), deterministic two-pass reduction

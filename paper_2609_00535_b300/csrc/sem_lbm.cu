@@ -296,16 +296,18 @@ struct Impl {
         s.moving ? s.wub : nullptr, s.wsf);
   }
   static void lap(sem_lbm& s) {
-    k_lap<L, NP, EPB><<<blocks(s), THREADS, SM_LAP, s.stream>>>(s.view, s.rho, s.lapr, s.drho);
+    launch(k_lap<L, NP, EPB>, blocks(s), THREADS, SM_LAP, s.stream, s.pdl, s.view, s.rho, s.lapr,
+           s.drho);
   }
   static void mu(sem_lbm& s) {
-    k_dss_mu<<<grid_of(s.G, kDssThreads), kDssThreads, 0, s.stream>>>(s.view, s.lapr, s.rho, s.mu);
+    launch(k_dss_mu, grid_of(s.G, kDssThreads), kDssThreads, 0, s.stream, s.pdl, s.view, s.lapr,
+           s.rho, s.mu);
   }
   static void force(sem_lbm& s) {
-    k_force<L, NP, EPB><<<blocks(s), THREADS, SM_FORCE, s.stream>>>(s.view);
+    launch(k_force<L, NP, EPB>, blocks(s), THREADS, SM_FORCE, s.stream, s.pdl, s.view);
   }
   static void collide(sem_lbm& s) {
-    k_dss_collide<L><<<grid_of(s.G, kDssThreads), kDssThreads, 0, s.stream>>>(s.view);
+    launch(k_dss_collide<L>, grid_of(s.G, kDssThreads), kDssThreads, 0, s.stream, s.pdl, s.view);
   }
   // small meshes: split the velocity pairs over up to NREP CTAs per element
   // batch until the grid reaches two CTAs per SM (1 = the unsplit kernel)
@@ -319,18 +321,18 @@ struct Impl {
     const int nb = blocks(s);
     const int P = rhs_split(s);
     if (P == 1)
-      k_rhs<L, NP, EPB, false><<<nb, THREADS, SM_RHS, s.stream>>>(s.view, gst);
+      launch(k_rhs<L, NP, EPB, false>, nb, THREADS, SM_RHS, s.stream, s.pdl, s.view, gst);
     else
-      k_rhs<L, NP, EPB, true><<<dim3(nb, P), THREADS, SM_RHS, s.stream>>>(s.view, gst);
+      launch(k_rhs<L, NP, EPB, true>, dim3(nb, P), THREADS, SM_RHS, s.stream, s.pdl, s.view, gst);
   }
   static void rk(sem_lbm& s, int stage, const double* gcur, double* out) {
     const int gr = grid_of(s.G, kDssThreads);
     if (stage == 1)
-      k_dss_rk<L, 1><<<gr, kDssThreads, 0, s.stream>>>(s.view, gcur, out);
+      launch(k_dss_rk<L, 1>, gr, kDssThreads, 0, s.stream, s.pdl, s.view, gcur, out);
     else if (stage == 2)
-      k_dss_rk<L, 2><<<gr, kDssThreads, 0, s.stream>>>(s.view, gcur, out);
+      launch(k_dss_rk<L, 2>, gr, kDssThreads, 0, s.stream, s.pdl, s.view, gcur, out);
     else
-      k_dss_rk<L, 3><<<gr, kDssThreads, 0, s.stream>>>(s.view, gcur, out);
+      launch(k_dss_rk<L, 3>, gr, kDssThreads, 0, s.stream, s.pdl, s.view, gcur, out);
   }
   static void diag(sem_lbm& s) {
     k_diag<L><<<s.diag_blocks, 256, 0, s.stream>>>(s.f, s.Me, s.parts, s.V);
@@ -387,11 +389,15 @@ enum { K_LAP = 0, K_MU, K_FORCE, K_COLLIDE, K_RHS, K_RK };
 // profiling hook: an event after each launch when per-kernel timing is on
 void mark(sem_lbm& s, int cls);
 
-// one full time step: collision, then three SSP-RK3 stages of streaming
-void enqueue_step(sem_lbm& s) {
+// one full time step: collision, then three SSP-RK3 stages of streaming.
+// With pdl, every kernel after the first is a programmatic dependent launch of
+// the one before it (the first follows whatever preceded the step normally).
+void enqueue_step(sem_lbm& s, bool pdl) {
   Ops& o = *s.ops;
   // rho and mu of fbar^n (rho is current: written by set_density/set_state or the last stage)
+  s.pdl = false;
   o.lap(s); mark(s, K_LAP);
+  s.pdl = pdl;
   o.mu(s); mark(s, K_MU);
   o.force(s); mark(s, K_FORCE);
   o.collide(s); mark(s, K_COLLIDE);          // fs = f* (RK base state U0)
@@ -403,9 +409,27 @@ void enqueue_step(sem_lbm& s) {
     o.rhs(s, s.g); mark(s, K_RHS);
     o.rk(s, stage, s.g, stage == 3 ? s.f : s.g); mark(s, K_RK);
   }
+  s.pdl = false;
 }
 
 int count_kernels_per_step() { return 6 + 2 * 4; }
+
+// capture one step into s.graph (programmatic dependent launches when pdl)
+int capture_step(sem_lbm& s, bool pdl) {
+  cudaGraph_t gr;
+  CUDA_TRY(cudaStreamBeginCapture(s.stream, cudaStreamCaptureModeThreadLocal));
+  enqueue_step(s, pdl);
+  cudaError_t e1 = cudaStreamEndCapture(s.stream, &gr);
+  if (e1 != cudaSuccess) return fail(SEMLBM_ECUDA, "graph capture: %s", cudaGetErrorString(e1));
+  cudaError_t e2 = cudaGraphInstantiate(&s.graph, gr, 0);
+  cudaGraphDestroy(gr);
+  if (e2 != cudaSuccess) {
+    s.graph = nullptr;
+    return fail(SEMLBM_ECUDA, "graph instantiate: %s", cudaGetErrorString(e2));
+  }
+  s.graph_pdl = pdl;
+  return 0;
+}
 
 bool record_event(sem_lbm& s, int cls) {
   if (s.nev == s.ev.size()) {
@@ -674,22 +698,18 @@ int sem_lbm_step(sem_lbm_t* s, int64_t n_steps) {
   DeviceGuard dg(s->device);
   if (s->prof_on) {
     if (s->nev == 0 && !record_event(*s, -1)) return fail(SEMLBM_ECUDA, "cudaEventRecord failed");
-    for (int64_t i = 0; i < n_steps; ++i) enqueue_step(*s);
+    for (int64_t i = 0; i < n_steps; ++i) enqueue_step(*s, false);   // events bracket each kernel
     CUDA_TRY(cudaGetLastError());
     s->step += n_steps;
     return 0;
   }
   if (!s->graph) {
-    cudaGraph_t gr;
-    CUDA_TRY(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
-    enqueue_step(*s);
-    cudaError_t e1 = cudaStreamEndCapture(s->stream, &gr);
-    if (e1 != cudaSuccess) return fail(SEMLBM_ECUDA, "graph capture: %s", cudaGetErrorString(e1));
-    cudaError_t e2 = cudaGraphInstantiate(&s->graph, gr, 0);
-    cudaGraphDestroy(gr);
-    if (e2 != cudaSuccess) {
-      s->graph = nullptr;
-      return fail(SEMLBM_ECUDA, "graph instantiate: %s", cudaGetErrorString(e2));
+    // with programmatic edges between the step's kernels first; should that
+    // capture or instantiation fail, the plain graph of the same kernels
+    int rc = capture_step(*s, true);
+    if (rc != 0) {
+      cudaGetLastError();
+      if ((rc = capture_step(*s, false)) != 0) return rc;
     }
   }
   for (int64_t i = 0; i < n_steps; ++i) CUDA_TRY(cudaGraphLaunch(s->graph, s->stream));
@@ -806,6 +826,7 @@ int sem_lbm_get_info(const sem_lbm_t* s, sem_lbm_info_t* out) {
   out->kernels_per_step = s->kernels_per_step;
   out->elements_per_cta = s->ops->epb;
   out->rhs_pair_groups = s->ops->rhs_split(*s);
+  out->graph_pdl = s->graph_pdl ? 1 : 0;
   return 0;
 }
 

@@ -5,6 +5,7 @@
 
 #include <cstdint>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "kernels.cuh"
@@ -18,6 +19,27 @@ int fail(int code, const char* fmt, ...);
 constexpr int kDssThreads = 128;   // threads per CTA of the gather-scatter kernels
 
 inline int grid_of(int64_t work, int threads) { return (int)((work + threads - 1) / threads); }
+
+// Launches a kernel, optionally as a programmatic dependent launch: the kernel
+// may then be scheduled while the previous kernel on the stream finishes, and
+// it waits for that kernel's completion (and the visibility of its writes) in
+// pdl_wait() before touching any data (kernels.cuh).  Inside a captured graph
+// the dependency becomes a programmatic edge.
+template <typename... KArgs, typename... Args>
+cudaError_t launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                   cudaStream_t stream, bool pdl, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // Makes `device` current for the lifetime of the guard and restores the
 // caller's device afterwards, so that a call on a solver or batch launches on
@@ -79,6 +101,8 @@ struct sem_lbm {
   cudaGraphExec_t graph = nullptr;
   int kernels_per_step = 0;
   bool prof_on = false;
+  bool pdl = false;                     // launch the step's kernels as programmatic dependents
+  bool graph_pdl = false;               // the captured step has programmatic edges
   sem_lbm_batch* batch = nullptr;     // set while a batch steps this solver
   cudaStream_t home_stream = nullptr; // the solver's own stream while it is in a batch
   std::vector<cudaEvent_t> ev;   // event pool; ev[0..nev) recorded since the last read

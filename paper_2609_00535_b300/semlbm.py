@@ -82,7 +82,8 @@ class InfoC(ctypes.Structure):
                 ("dt", ctypes.c_double), ("kappa", ctypes.c_double), ("beta", ctypes.c_double),
                 ("tau", ctypes.c_double), ("workspace_bytes", ctypes.c_size_t),
                 ("graph_launches", ctypes.c_int), ("kernels_per_step", ctypes.c_int),
-                ("elements_per_cta", ctypes.c_int), ("rhs_pair_groups", ctypes.c_int)]
+                ("elements_per_cta", ctypes.c_int), ("rhs_pair_groups", ctypes.c_int),
+                ("graph_pdl", ctypes.c_int)]
 
 
 class GroupInfoC(ctypes.Structure):
