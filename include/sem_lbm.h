@@ -124,7 +124,9 @@ typedef struct {
   double umax;        /* max |u|                                               */
   double rho_min, rho_max;
   int64_t n_nonfinite;/* non-finite entries of fbar                            */
-  int status;         /* SEMLBM_OK or SEMLBM_ENONFINITE                        */
+  int status;         /* SEMLBM_OK, SEMLBM_ENONFINITE, or SEMLBM_ETIMEOUT when a
+                         streaming kernel's bounded wait for its bulk-copied tiles
+                         gave up (the step's results are then not valid)      */
 } sem_lbm_diag;
 
 typedef struct {

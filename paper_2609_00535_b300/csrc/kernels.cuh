@@ -106,6 +106,47 @@ __device__ __forceinline__ void stage_in(double* __restrict__ s, const double* _
   for (int i = threadIdx.x; i < count; i += blockDim.x) s[i] = __ldg(g + base + i);
 }
 
+// Tile staging by the bulk-copy engine (cp.async.bulk, the one-dimensional form
+// of TMA, sm_90 and later): thread 0 starts `ntiles` copies of `count` doubles,
+// tile t from src(t) (global) to dst(t) (shared), all completing on one
+// mbarrier, and every thread of the CTA waits for their bytes.  The caller
+// guarantees 16-byte aligned sources, destinations and sizes (count even).  The
+// wait is bounded: after kBulkWaitPolls polls it sets flags[2] (reported as
+// SEMLBM_ETIMEOUT) and returns, so a copy that never lands cannot hang the GPU.
+// One use per CTA lifetime (the barrier is initialised here, phase 0).
+constexpr int kBulkWaitPolls = 1 << 22;
+
+template <class Tile>
+__device__ __forceinline__ void stage_bulk(int ntiles, int count, Tile tile, int* flags) {
+  __shared__ alignas(8) unsigned long long bar;
+  const unsigned mb = (unsigned)__cvta_generic_to_shared(&bar);
+  const unsigned bytes = (unsigned)count * 8u;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb),
+                 "r"(bytes * (unsigned)ntiles) : "memory");
+    for (int t = 0; t < ntiles; ++t) {
+      double* dst;
+      const double* src;
+      tile(t, dst, src);
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+              "r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src), "r"(bytes), "r"(mb)
+          : "memory");
+    }
+  }
+  __syncthreads();   // the barrier is initialised before anyone polls it
+  unsigned done = 0;
+  for (int it = 0; it < kBulkWaitPolls && !done; ++it)
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(done)
+        : "r"(mb), "r"(0u)
+        : "memory");
+  if (!done) atomicOr(flags + 2, 1);
+}
+
 // Programmatic dependent launch (sm_90 and later): a kernel launched with the
 // programmatic-serialization attribute may start while its predecessor on the
 // stream is still running; pdl_wait() blocks until the predecessor has
@@ -538,7 +579,8 @@ __device__ __forceinline__ void body_dss_collide(const View& v, int g) {
 // pairs a CTA computes, so splitting the pairs over CTAs gives the same bits
 template <class L, int NP, int EPB, bool SPLIT = false>
 __device__ __forceinline__ void body_rhs(const View& v, const double* __restrict__ gst, int eb,
-                                         double* sm, int pr0 = 0, int pr1 = L::NREP) {
+                                         double* sm, int pr0 = 0, int pr1 = L::NREP,
+                                         bool bulk = false) {
   constexpr int D = L::D, Q = L::Q, NL = ipow(NP, D), NT = EPB * NL;
   const int64_t V = v.V;
   const int E = v.E;
@@ -556,12 +598,31 @@ __device__ __forceinline__ void body_rhs(const View& v, const double* __restrict
   const int count = min(EPB, E - e0) * NL;
   const int64_t base = (int64_t)e0 * NL;
   for (int i = threadIdx.x; i < NP * NP; i += blockDim.x) sD[i] = __ldg(Dmat + i);
-  stage_in(sr, v.rho, base, count);
-  stage_in(smu, v.mu, base, count);
+  // the rho, mu and Q-1 velocity tiles: by bulk copies when every tile is 16-byte
+  // aligned (an even node offset, plane length and count, and aligned shared
+  // tiles), else by the load loop
+  bool staged = false;
+  if constexpr (!SPLIT && (NP * NP) % 2 == 0 && NT % 2 == 0) {
+    if (bulk && ((base | V | (int64_t)count) & 1) == 0 &&
+        (((unsigned)__cvta_generic_to_shared(sr) | (unsigned)__cvta_generic_to_shared(sg)) & 15) == 0) {
+      stage_bulk(Q + 1, count, [&](int t, double*& dst, const double*& src) {
+        if (t == 0) { dst = sr; src = v.rho + base; }
+        else if (t == 1) { dst = smu; src = v.mu + base; }
+        else { dst = sg + (t - 2) * NT; src = gst + (t - 1) * V + base; }
+      }, v.flags);
+      staged = true;
+    }
+  }
   if constexpr (!SPLIT) {
+    if (!staged) {
+      stage_in(sr, v.rho, base, count);
+      stage_in(smu, v.mu, base, count);
 #pragma unroll 1
-    for (int q = 1; q < Q; ++q) stage_in(sg + (q - 1) * NT, gst + q * V, base, count);
+      for (int q = 1; q < Q; ++q) stage_in(sg + (q - 1) * NT, gst + q * V, base, count);
+    }
   } else {
+    stage_in(sr, v.rho, base, count);
+    stage_in(smu, v.mu, base, count);
 #pragma unroll 1
     for (int p = pr0; p < pr1; ++p) {
       const int A = L::rep(p), B = L::opp(A);
@@ -791,13 +852,13 @@ __global__ void __launch_bounds__(cta_threads<L::D, NP, EPB>(), rhs_min_blocks<L
     k_rhs(View v, const double* __restrict__ gst) {
   // SPLIT: the velocity pairs of each element batch are spread over gridDim.y
   // CTAs (meshes too small to fill the GPU with one CTA per element batch)
-  extern __shared__ double sm[];
+  extern __shared__ __align__(128) double sm[];
   pdl_wait();
   if constexpr (SPLIT) {
     const int P = gridDim.y, y = blockIdx.y;
     body_rhs<L, NP, EPB, true>(v, gst, blockIdx.x, sm, y * L::NREP / P, (y + 1) * L::NREP / P);
   } else {
-    body_rhs<L, NP, EPB>(v, gst, blockIdx.x, sm);
+    body_rhs<L, NP, EPB>(v, gst, blockIdx.x, sm, 0, L::NREP, true);   // one element batch: bulk staging
   }
   pdl_trigger();
 }

@@ -724,7 +724,7 @@ int sem_lbm_diagnostics(sem_lbm_t* s, sem_lbm_diag* out) {
   s->ops->diag(*s);
   CUDA_TRY(cudaGetLastError());
   DiagPart d;
-  int flags[2];
+  int flags[3];   // [1] non-finite stage state, [2] a bounded tile-staging wait gave up
   CUDA_TRY(cudaMemcpyAsync(&d, s->dout, sizeof d, cudaMemcpyDeviceToHost, s->stream));
   CUDA_TRY(cudaMemcpyAsync(flags, s->flags, sizeof flags, cudaMemcpyDeviceToHost, s->stream));
   CUDA_TRY(cudaStreamSynchronize(s->stream));
@@ -737,7 +737,9 @@ int sem_lbm_diagnostics(sem_lbm_t* s, sem_lbm_diag* out) {
   out->rho_min = d.rho_min;
   out->rho_max = d.rho_max;
   out->n_nonfinite = (int64_t)d.nonfinite;
-  out->status = (d.nonfinite > 0 || flags[1]) ? SEMLBM_ENONFINITE : SEMLBM_OK;
+  out->status = (d.nonfinite > 0 || flags[1]) ? SEMLBM_ENONFINITE
+                 : flags[2]                     ? SEMLBM_ETIMEOUT
+                                                : SEMLBM_OK;
   return 0;
 }
 
