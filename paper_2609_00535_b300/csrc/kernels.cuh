@@ -147,6 +147,32 @@ __device__ __forceinline__ void stage_bulk(int ntiles, int count, Tile tile, int
   if (!done) atomicOr(flags + 2, 1);
 }
 
+// Stages ntiles element tiles of `count` doubles each (tile(t, dst, src) names
+// tile t): by bulk copies when `bulk` is set and every source, destination and
+// size is 16-byte aligned (the same decision on every thread of the CTA), else
+// by the load loop.  The caller synchronises the CTA before reading the tiles.
+template <class Tile>
+__device__ __forceinline__ void stage_tiles(bool bulk, int ntiles, int count, Tile tile,
+                                            int* flags) {
+  bool ok = bulk && (count & 1) == 0;
+  for (int t = 0; t < ntiles && ok; ++t) {
+    double* dst;
+    const double* src;
+    tile(t, dst, src);
+    ok = ((reinterpret_cast<uintptr_t>(src) | (unsigned)__cvta_generic_to_shared(dst)) & 15) == 0;
+  }
+  if (ok) {
+    stage_bulk(ntiles, count, tile, flags);
+    return;
+  }
+  for (int t = 0; t < ntiles; ++t) {
+    double* dst;
+    const double* src;
+    tile(t, dst, src);
+    for (int i = threadIdx.x; i < count; i += blockDim.x) dst[i] = __ldg(src + i);
+  }
+}
+
 // Programmatic dependent launch (sm_90 and later): a kernel launched with the
 // programmatic-serialization attribute may start while its predecessor on the
 // stream is still running; pdl_wait() blocks until the predecessor has
@@ -355,7 +381,7 @@ struct View {
 template <class L, int NP, int EPB>
 __device__ __forceinline__ void body_lap(const View& v, const double* __restrict__ rho,
                                          double* __restrict__ out, double* __restrict__ drho,
-                                         int eb, double* sm) {
+                                         int eb, double* sm, bool bulk = false) {
   constexpr int D = L::D, NL = ipow(NP, D), NT = EPB * NL;
   const int64_t V = v.V;
   const int E = v.E;
@@ -371,7 +397,10 @@ __device__ __forceinline__ void body_lap(const View& v, const double* __restrict
   const int count = min(EPB, E - e0) * NL;
   const int64_t base = (int64_t)e0 * NL;
   for (int i = threadIdx.x; i < NP * NP; i += blockDim.x) sD[i] = __ldg(Dmat + i);
-  stage_in(sr, rho, base, count);
+  stage_tiles(bulk, 1, count, [&](int, double*& dst, const double*& src) {
+    dst = sr;
+    src = rho + base;
+  }, v.flags);
   __syncthreads();
   const int tid = threadIdx.x;
   const bool act = tid < count;
@@ -439,7 +468,7 @@ __device__ __forceinline__ void body_dss_mu(const View& v, const double* __restr
 
 // a4 (part 1): element-local force M_e (c_s^2 grad rho - rho grad mu) (Sec. 2.1)
 template <class L, int NP, int EPB>
-__device__ __forceinline__ void body_force(const View& v, int eb, double* sm) {
+__device__ __forceinline__ void body_force(const View& v, int eb, double* sm, bool bulk = false) {
   constexpr int D = L::D, NL = ipow(NP, D), NT = EPB * NL;
   const int64_t V = v.V;
   const int E = v.E;
@@ -453,8 +482,10 @@ __device__ __forceinline__ void body_force(const View& v, int eb, double* sm) {
   const int count = min(EPB, E - e0) * NL;
   const int64_t base = (int64_t)e0 * NL;
   for (int i = threadIdx.x; i < NP * NP; i += blockDim.x) sD[i] = __ldg(Dmat + i);
-  stage_in(sr, v.rho, base, count);
-  stage_in(smu, v.mu, base, count);
+  stage_tiles(bulk, 2, count, [&](int t, double*& dst, const double*& src) {
+    dst = t == 0 ? sr : smu;
+    src = (t == 0 ? v.rho : v.mu) + base;
+  }, v.flags);
   __syncthreads();
   const int tid = threadIdx.x;
   if (tid < count) {
@@ -598,28 +629,12 @@ __device__ __forceinline__ void body_rhs(const View& v, const double* __restrict
   const int count = min(EPB, E - e0) * NL;
   const int64_t base = (int64_t)e0 * NL;
   for (int i = threadIdx.x; i < NP * NP; i += blockDim.x) sD[i] = __ldg(Dmat + i);
-  // the rho, mu and Q-1 velocity tiles: by bulk copies when every tile is 16-byte
-  // aligned (an even node offset, plane length and count, and aligned shared
-  // tiles), else by the load loop
-  bool staged = false;
-  if constexpr (!SPLIT && (NP * NP) % 2 == 0 && NT % 2 == 0) {
-    if (bulk && ((base | V | (int64_t)count) & 1) == 0 &&
-        (((unsigned)__cvta_generic_to_shared(sr) | (unsigned)__cvta_generic_to_shared(sg)) & 15) == 0) {
-      stage_bulk(Q + 1, count, [&](int t, double*& dst, const double*& src) {
-        if (t == 0) { dst = sr; src = v.rho + base; }
-        else if (t == 1) { dst = smu; src = v.mu + base; }
-        else { dst = sg + (t - 2) * NT; src = gst + (t - 1) * V + base; }
-      }, v.flags);
-      staged = true;
-    }
-  }
-  if constexpr (!SPLIT) {
-    if (!staged) {
-      stage_in(sr, v.rho, base, count);
-      stage_in(smu, v.mu, base, count);
-#pragma unroll 1
-      for (int q = 1; q < Q; ++q) stage_in(sg + (q - 1) * NT, gst + q * V, base, count);
-    }
+  if constexpr (!SPLIT) {   // rho, mu and the Q-1 moving velocities
+    stage_tiles(bulk, Q + 1, count, [&](int t, double*& dst, const double*& src) {
+      if (t == 0) { dst = sr; src = v.rho + base; }
+      else if (t == 1) { dst = smu; src = v.mu + base; }
+      else { dst = sg + (t - 2) * NT; src = gst + (t - 1) * V + base; }
+    }, v.flags);
   } else {
     stage_in(sr, v.rho, base, count);
     stage_in(smu, v.mu, base, count);
@@ -821,7 +836,7 @@ __global__ void __launch_bounds__(cta_threads<L::D, NP, EPB>())
           double* __restrict__ drho) {
   extern __shared__ double sm[];
   pdl_wait();
-  body_lap<L, NP, EPB>(v, rho, out, drho, blockIdx.x, sm);
+  body_lap<L, NP, EPB>(v, rho, out, drho, blockIdx.x, sm);   // one tile: the load loop
   pdl_trigger();
 }
 
@@ -836,7 +851,7 @@ template <class L, int NP, int EPB>
 __global__ void __launch_bounds__(cta_threads<L::D, NP, EPB>()) k_force(View v) {
   extern __shared__ double sm[];
   pdl_wait();
-  body_force<L, NP, EPB>(v, blockIdx.x, sm);
+  body_force<L, NP, EPB>(v, blockIdx.x, sm);   // two tiles: the load loop
   pdl_trigger();
 }
 
