@@ -550,7 +550,9 @@ def native_arm(args):
 
     # timed region: K steps, every kernel bracketed by CUDA events on the
     # solver's stream (per-kernel durations for the roofline)
-    solver.profile(True)
+    # timed region: K steps replayed from the captured graph, as a user's
+    # sem_lbm_step runs them (programmatic launches, no events between kernels),
+    # bracketed by CUDA events on the solver's stream
     clocks = Clocks(device)
     barrier()
     torch.cuda.synchronize()
@@ -564,8 +566,20 @@ def native_arm(args):
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
-    clk = clocks.stop()
     ms = e0.elapsed_time(e1)
+    # the same K steps again with a CUDA event after every kernel
+    # (sem_lbm_profile): the per-kernel durations of the roofline and the shares
+    solver.profile(True)
+    p0 = torch.cuda.Event(enable_timing=True)
+    p1 = torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for _ in range(args.steps):
+        solver.step(1)
+    p1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    prof_ms = p0.elapsed_time(p1) / args.steps
     prof = solver.profile_read()
     solver.profile(False)
     ms = max_over_ranks(ms, device="cuda")
@@ -674,7 +688,11 @@ def native_arm(args):
             "kernel_share": shares,
             "kernel_ms_per_launch": {k: round(prof["ms"][k] / max(1, prof["launches"][k]), 4)
                                      for k in prof["ms"]},
-            "gpu_launches": int(sum(prof["launches"].values())),
+            "gpu_launches": int(info["kernels_per_step"] * args.steps),
+            "graph_programmatic_launches": bool(solver.get_info()["graph_pdl"]),
+            "instrumented": {"ms_per_step": prof_ms, "node_updates_per_s": V / (prof_ms * 1e-3),
+                             "note": "the same K steps issued kernel by kernel with a CUDA event "
+                                     "after each (source of the roofline and the kernel shares)"},
             "clocks": clk,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": Q * V * 8,
                     "d2h_bytes_per_step": 80, "steps": e2e_steps},

@@ -100,6 +100,42 @@ def test_cylinder_contact_angle(deg):
     assert abs(th_dev - deg) < 4.0 and abs(th_dev - th) < 5.0, (deg, th, th_dev)
 
 
+def test_cylinder_contact_angle_thinner_interface():
+    """The cylinder case at half the interface width (delta / R = 0.2: O-grid
+    96x20, N = 6, delta = 0.03), 60 and 120 degrees in one batch for 6e4 steps: the
+    contour circle fit and the device moments agree with each other and with the
+    prescribed angle to within 3 degrees (at delta / R = 0.4 the 120-degree drop's
+    two estimates differ by 4.2 degrees)."""
+    from paper_2609_00535_b300 import semlbm
+    Rc = Rd = 0.15
+    delta = 0.03
+    m = inputs.rotate_elements(inputs.cylinder_ogrid(6, n_theta=96, n_r=20, Rc=Rc), 2)
+    b = semlbm.Batch()
+    runs = {}
+    for deg in (60, 120):
+        c = make_case("cyl2", m, "D2Q9", 0.1, delta, 1.0, math.radians(deg),
+                      rho0=inputs.cylinder_cap_density(m, (0.5, 0.5), Rc, Rd, math.radians(deg), delta))
+        s = semlbm.Solver.from_case(c)
+        s.set_density(c.rho0)
+        runs[b.add(s)] = (deg, s)
+    b.step(60000)
+    d = b.diagnostics()
+    for slot, (deg, s) in runs.items():
+        assert d[slot]["status"] == 0
+        rho = s.field("rho")
+        p = contour_points(m.node_xyz, rho.reshape(m.n_elem, -1), 0.55, 7)
+        p = p[np.linalg.norm(p - 0.5, axis=1) > Rc + delta]
+        cx, cy, R = fit_circle(p)
+        dist = math.hypot(cx - 0.5, cy - 0.5)
+        th = math.degrees(math.acos((Rc ** 2 + R ** 2 - dist ** 2) / (2 * Rc * R)))
+        th_dev = wetting.contact_angle(s.wetting_moments(0), 2, delta=delta, wall_radius=Rc)
+        assert abs(th - deg) < 3.0 and abs(th_dev - deg) < 3.0 and abs(th - th_dev) < 3.0, \
+            (deg, th, th_dev)
+    b.close()
+    for _, s in runs.values():
+        s.close()
+
+
 @pytest.mark.parametrize("R", [0.25, 0.3])
 def test_laplace_law_and_residual_kinetic_energy(R):
     m = inputs.box((8, 8), (0, 0), (1, 1), 4, face_tags={0: -1, 1: -1, 2: -1, 3: -1})
