@@ -35,11 +35,11 @@ import hashlib  # noqa: E402
 METRIC = "FP64 GLL node-updates/s (3D droplet)"
 
 # DRAM traffic of one k_rhs launch from an ncu capture of the 12^3-hex
-# sphere-cap mesh at N = 5 (373,248 nodes: 82.17 MB read + 5.56 MB written);
-# the traffic grows with the node count, so it is scaled per node.  Valid only
-# while the kernel sources are the ones profiled.
-RHS_TRAFFIC = {"kernels.cuh": "acc0fb11982f92c5", "lattice.cuh": "2210c9bd29fce6f9",
-               "bytes_per_node": (82.17e6 + 5.56e6) / 373248, "lattice": "D3Q13", "N": 5}
+# sphere-cap mesh at N = 5 (373,248 nodes: 82.14 MB read + 4.20 MB written, the
+# mean of two launches); the traffic grows with the node count, so it is scaled
+# per node.  Valid only while the kernel sources are the ones profiled.
+RHS_TRAFFIC = {"kernels.cuh": "edcb6377d1397c66", "lattice.cuh": "2210c9bd29fce6f9",
+               "bytes_per_node": (82.14e6 + 4.20e6) / 373248, "lattice": "D3Q13", "N": 5}
 
 
 def rhs_traffic_per_launch(lattice, N, n_local):

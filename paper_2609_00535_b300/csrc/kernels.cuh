@@ -112,8 +112,10 @@ __device__ __forceinline__ void stage_in(double* __restrict__ s, const double* _
 // mbarrier, and every thread of the CTA waits for their bytes.  The caller
 // guarantees 16-byte aligned sources, destinations and sizes (count even).  The
 // wait is bounded: after kBulkWaitPolls polls it sets flags[2] (reported as
-// SEMLBM_ETIMEOUT) and returns, so a copy that never lands cannot hang the GPU.
-// One use per CTA lifetime (the barrier is initialised here, phase 0).
+// SEMLBM_ETIMEOUT), waits once more with the same bound for the copies still in
+// flight into this CTA's shared memory, and returns, so a copy that never lands
+// cannot hang the GPU.  One use per CTA lifetime (the barrier is initialised
+// here, phase 0).
 constexpr int kBulkWaitPolls = 1 << 22;
 
 template <class Tile>
@@ -137,14 +139,20 @@ __device__ __forceinline__ void stage_bulk(int ntiles, int count, Tile tile, int
     }
   }
   __syncthreads();   // the barrier is initialised before anyone polls it
-  unsigned done = 0;
-  for (int it = 0; it < kBulkWaitPolls && !done; ++it)
-    asm volatile(
-        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
-        : "=r"(done)
-        : "r"(mb), "r"(0u)
-        : "memory");
-  if (!done) atomicOr(flags + 2, 1);
+  auto wait = [&]() {
+    unsigned done = 0;
+    for (int it = 0; it < kBulkWaitPolls && !done; ++it)
+      asm volatile(
+          "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+          : "=r"(done)
+          : "r"(mb), "r"(0u)
+          : "memory");
+    return done != 0;
+  };
+  if (!wait()) {
+    atomicOr(flags + 2, 1);
+    wait();   // the copies in flight, before the CTA reuses or releases its tiles
+  }
 }
 
 // Stages ntiles element tiles of `count` doubles each (tile(t, dst, src) names
@@ -602,50 +610,22 @@ __device__ __forceinline__ void body_dss_collide(const View& v, int g) {
   }
 }
 
-// a5: element-local right-hand side of the force-split streaming (Sec. 3.3)
+// a5: the element-local right-hand side of one element batch from its staged
+// tiles (sD: D; sr, smu: rho and mu; sg: the moving velocities, [Q-1][NT]) for
+// the opposite-velocity pairs [pr0, pr1) when SPLIT (all pairs otherwise)
 //   r_a = M_e [ -e_a . grad(g_a - t_a rho) - (t_a/c_s^2) rho e_a . grad(mu) ]
 //         + flux bounce-back on incoming wall directions (Sec. 2.2)
-// for the opposite-velocity pairs [pr0, pr1) of the velocity set when SPLIT
-// (all pairs otherwise); a pair's two values do not depend on which other
-// pairs a CTA computes, so splitting the pairs over CTAs gives the same bits
-template <class L, int NP, int EPB, bool SPLIT = false>
-__device__ __forceinline__ void body_rhs(const View& v, const double* __restrict__ gst, int eb,
-                                         double* sm, int pr0 = 0, int pr1 = L::NREP,
-                                         bool bulk = false) {
+template <class L, int NP, int EPB, bool SPLIT>
+__device__ __forceinline__ void rhs_compute(const View& v, const double* sD, const double* sr,
+                                            const double* smu, const double* sg, int count,
+                                            int64_t base, int pr0, int pr1) {
   constexpr int D = L::D, Q = L::Q, NL = ipow(NP, D), NT = EPB * NL;
   const int64_t V = v.V;
-  const int E = v.E;
   const double* __restrict__ MJ = v.MJ;
-  const double* __restrict__ Dmat = v.Dm;
   const int* __restrict__ wslot = v.wslot;
   const double* __restrict__ wae = v.ae;
   const int R = v.R;
   double* __restrict__ r = v.r;
-  double* sD = sm;
-  double* sr = sD + NP * NP;
-  double* smu = sr + NT;
-  double* sg = smu + NT;   // [Q-1][NT], moving directions only
-  const int e0 = eb * EPB;
-  const int count = min(EPB, E - e0) * NL;
-  const int64_t base = (int64_t)e0 * NL;
-  for (int i = threadIdx.x; i < NP * NP; i += blockDim.x) sD[i] = __ldg(Dmat + i);
-  if constexpr (!SPLIT) {   // rho, mu and the Q-1 moving velocities
-    stage_tiles(bulk, Q + 1, count, [&](int t, double*& dst, const double*& src) {
-      if (t == 0) { dst = sr; src = v.rho + base; }
-      else if (t == 1) { dst = smu; src = v.mu + base; }
-      else { dst = sg + (t - 2) * NT; src = gst + (t - 1) * V + base; }
-    }, v.flags);
-  } else {
-    stage_in(sr, v.rho, base, count);
-    stage_in(smu, v.mu, base, count);
-#pragma unroll 1
-    for (int p = pr0; p < pr1; ++p) {
-      const int A = L::rep(p), B = L::opp(A);
-      stage_in(sg + (A - 1) * NT, gst + A * V, base, count);
-      stage_in(sg + (B - 1) * NT, gst + B * V, base, count);
-    }
-  }
-  __syncthreads();
   const int tid = threadIdx.x;
   if (tid >= count) return;
   const int le = tid / NL, k = tid - le * NL, lb = le * NL;
@@ -706,6 +686,47 @@ __device__ __forceinline__ void body_rhs(const View& v, const double* __restrict
     // node-major partials: the pair's two values side by side (one 16-byte store)
     reinterpret_cast<double2*>(r + idx * (Q - 1))[decltype(RR)::value] = make_double2(rA, rB);
   });
+}
+
+// a5: element-local right-hand side of the force-split streaming (Sec. 3.3) for
+// element batch eb: stage its tiles, then rhs_compute.  For the
+// opposite-velocity pairs [pr0, pr1) of the velocity set when SPLIT (all pairs
+// otherwise); a pair's two values do not depend on which other pairs a CTA
+// computes, so splitting the pairs over CTAs gives the same bits
+template <class L, int NP, int EPB, bool SPLIT = false>
+__device__ __forceinline__ void body_rhs(const View& v, const double* __restrict__ gst, int eb,
+                                         double* sm, int pr0 = 0, int pr1 = L::NREP,
+                                         bool bulk = false) {
+  constexpr int D = L::D, Q = L::Q, NL = ipow(NP, D), NT = EPB * NL;
+  const int64_t V = v.V;
+  const int E = v.E;
+  const double* __restrict__ Dmat = v.Dm;
+  double* sD = sm;
+  double* sr = sD + NP * NP;
+  double* smu = sr + NT;
+  double* sg = smu + NT;   // [Q-1][NT], moving directions only
+  const int e0 = eb * EPB;
+  const int count = min(EPB, E - e0) * NL;
+  const int64_t base = (int64_t)e0 * NL;
+  for (int i = threadIdx.x; i < NP * NP; i += blockDim.x) sD[i] = __ldg(Dmat + i);
+  if constexpr (!SPLIT) {   // rho, mu and the Q-1 moving velocities
+    stage_tiles(bulk, Q + 1, count, [&](int t, double*& dst, const double*& src) {
+      if (t == 0) { dst = sr; src = v.rho + base; }
+      else if (t == 1) { dst = smu; src = v.mu + base; }
+      else { dst = sg + (t - 2) * NT; src = gst + (t - 1) * V + base; }
+    }, v.flags);
+  } else {
+    stage_in(sr, v.rho, base, count);
+    stage_in(smu, v.mu, base, count);
+#pragma unroll 1
+    for (int p = pr0; p < pr1; ++p) {
+      const int A = L::rep(p), B = L::opp(A);
+      stage_in(sg + (A - 1) * NT, gst + A * V, base, count);
+      stage_in(sg + (B - 1) * NT, gst + B * V, base, count);
+    }
+  }
+  __syncthreads();
+  rhs_compute<L, NP, EPB, SPLIT>(v, sD, sr, smu, sg, count, base, pr0, pr1);
 }
 
 // SSP-RK3 stage value from the base state u0, the current stage state gc and

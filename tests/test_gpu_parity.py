@@ -85,11 +85,18 @@ def test_sphere_cap_d3q13_1000_steps():
 
 def test_unsplit_rhs_kernel_against_oracle():
     """320 hexes at N = 5 give more element batches than two per SM, so the
-    single-solve step launches k_rhs with one CTA per element batch: the kernel
-    variant that the sphere benchmark times (the smaller meshes above take the
-    pair-split variant)."""
+    single-solve step launches k_rhs with one CTA per element batch and its
+    tiles staged by bulk copies: the kernel variant that the sphere benchmark
+    times (the smaller meshes above take the pair-split variant)."""
     case = inputs.sphere_3d(N=5, ne=(8, 8, 5))
     _compare(case, 20, rhs_pair_groups=1)
+
+
+def test_unsplit_rhs_odd_tile_against_oracle():
+    """343 hexes at N = 6: the unsplit k_rhs on an odd element tile (343 nodes),
+    whose tiles are not 16-byte aligned and are staged by the load loop."""
+    case = inputs.sphere_3d(N=6, ne=(7, 7, 7))
+    _compare(case, 10, rhs_pair_groups=1)
 
 
 def test_benchmark_workload_full_size():
