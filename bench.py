@@ -312,7 +312,9 @@ def serving_section(args, device, capacity):
     n = args.serve_requests
     probe = inputs.relaxing_request_stream(n=n, rate=1.0, seed=8)
     nodes = [r.case().nodes for r in probe]
-    work = sum(nodes) / len(nodes) * 0.5 * args.serve_max_steps
+    # mean work per request: its nodes times the mean steps to converge (the
+    # kinds' medians, 5e3 to 1.2e5 steps, average about a quarter of the budget)
+    work = sum(nodes) / len(nodes) * 0.25 * args.serve_max_steps
     rate = 1.2 * capacity / work              # offered load ~1.2x the measured capacity
     reqs = inputs.relaxing_request_stream(n=n, rate=rate, seed=8)
     srv = serve.Server(hbm_budget_bytes=int(args.serve_budget_gb * 2 ** 30),
@@ -733,7 +735,7 @@ def main():
     ap.add_argument("--cpu-sample-steps", type=int, default=60,
                     help="oracle steps per core replica of the bounded sample")
     ap.add_argument("--serve-requests", type=int, default=100)
-    ap.add_argument("--serve-max-steps", type=int, default=100000)
+    ap.add_argument("--serve-max-steps", type=int, default=200000)
     ap.add_argument("--serve-epoch", type=int, default=500)
     ap.add_argument("--serve-budget-gb", type=float, default=40.0)
     ap.add_argument("--sweep-requests", type=int, default=16)

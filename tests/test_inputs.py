@@ -152,3 +152,4 @@ def test_relaxing_request_stream():
         assert c.rho0.max() > 0.85 and abs(c.rho0.min() - c.rho_v) < 2e-3   # a drop in vapour
     assert inputs.viscous_tau(0.01, 1.0, steps=1e4) == pytest.approx(3.0)
     assert inputs.viscous_tau(0.1, 1.0) == 1.0
+    assert inputs.viscous_tau(1e-3, 1.0) == 10.0          # capped
