@@ -350,6 +350,29 @@ def serving_section(args, device, capacity):
     return out
 
 
+def serving_c5_sizes_section(args, device, capacity):
+    """Admission and continuous batching at the mesh sizes of the survey's C5
+    stream (E log-uniform in [256, 8192], N in 4..7; a quarter each flat wall,
+    cylinder, sphere cap and periodic drop 2D/3D), each request capped at a few
+    hundred steps: these sizes relax too slowly to run to KE_max < 1e-20 here, so
+    this measures admission by HBM budget and throughput under load, not
+    time-to-converged."""
+    from paper_2609_00535_b300 import serve
+    n = args.c5_requests
+    probe = inputs.request_stream(n=n, rate=1.0, seed=5)
+    nodes = [r.E * (r.N + 1) ** (3 if "3d" in r.kind else 2) for r in probe]
+    rate = 1.2 * capacity / (sum(nodes) / len(nodes) * args.c5_steps)
+    reqs = inputs.request_stream(n=n, rate=rate, seed=5)
+    srv = serve.Server(hbm_budget_bytes=int(args.serve_budget_gb * 2 ** 30), epoch_steps=50,
+                       ke_tol=1e-20, max_steps=args.c5_steps, min_steps=50)
+    out = srv.run(reqs).summary()
+    out.update({"workload": "C5 sizes: E log-uniform in [256, 8192], N 4..7, capped at %d "
+                            "steps (admission and throughput, not convergence)" % args.c5_steps,
+                "arrival_rate_per_s": rate, "offered_load": 1.2, "max_steps": args.c5_steps,
+                "hbm_budget_gb": args.serve_budget_gb})
+    return out
+
+
 def angle_sweep_section(args, device):
     """Contact-angle sweep through the server: drops on a flat wall run until
     KE_max < 1e-20, each started at its equilibrium cap and, as a comparison
@@ -656,10 +679,11 @@ def native_arm(args):
         lattices = None if args.no_lattices else lattice_section(args, device)
         angle_study = angle_resolution_section(args, device) if args.angle_study else None
         configs = None if args.no_configs else config_lines_section(args, device)
-        sweep = None
+        sweep = serving_c5 = None
         if not args.no_serving:
             cap = batched["batched_node_updates_per_s"] if batched else value
             serving = serving_section(args, device, cap)
+            serving_c5 = serving_c5_sizes_section(args, device, cap)
             sweep = angle_sweep_section(args, device)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -704,6 +728,7 @@ def native_arm(args):
             "batched": batched,
             "batched_small": batched_small,
             "serving": serving,
+            "serving_c5_sizes": serving_c5,
             "angle_sweep": sweep,
             "lattices": lattices,
             "angle_resolution": angle_study,
@@ -739,6 +764,8 @@ def main():
     ap.add_argument("--serve-epoch", type=int, default=500)
     ap.add_argument("--serve-budget-gb", type=float, default=40.0)
     ap.add_argument("--sweep-requests", type=int, default=16)
+    ap.add_argument("--c5-requests", type=int, default=60)
+    ap.add_argument("--c5-steps", type=int, default=300)
     ap.add_argument("--lattice-steps", type=int, default=50)
     ap.add_argument("--angle-study", action="store_true",
                     help="flat-wall contact angle at three interface widths (minutes)")

@@ -75,3 +75,27 @@ def test_requests_run_to_convergence():
         assert np.array_equal(s.get_state()[0], rec.state), rec.name
         assert s.diagnostics()["ke_max"] < 1e-20
         s.close()
+
+
+def test_relaxing_requests_converge():
+    """One request of each relaxing kind (flat wall, cylinder, sphere wall,
+    periodic drop 2D and 3D), served together, each retires on KE_max < 1e-20
+    within its step budget; the served state of the first equals its solo run."""
+    from paper_2609_00535_b300 import semlbm
+    kinds = [("relaxflat2d", 32), ("relaxcyl2d", 72), ("relaxsphere3d", 27), ("relaxdrop2d", 16),
+             ("relaxdrop3d", 27)]
+    reqs = [inputs.Request(i, 0.01 * i, k, E, 4, math.radians(60 + 20 * i), 1.0, 300 + i)
+            for i, (k, E) in enumerate(kinds)]
+    st = Server(hbm_budget_bytes=2 << 30, epoch_steps=1000, ke_tol=1e-20, max_steps=200000,
+                min_steps=1000, keep_state=True).run(reqs)
+    summ = st.summary()
+    assert summ["completed"] == 5 and summ["converged"] == 5, [(r.name, r.steps, r.ke_max)
+                                                               for r in st.records]
+    rec = st.records[0]
+    case = reqs[0].case()
+    s = semlbm.Solver.from_case(case)
+    s.set_density(case.rho0)
+    s.step(rec.steps)
+    assert np.array_equal(s.get_state()[0], rec.state)
+    assert s.diagnostics()["ke_max"] < 1e-20
+    s.close()
