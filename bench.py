@@ -456,6 +456,11 @@ def config_lines_section(args, device):
                      "k_rhs_pair_groups": info["rhs_pair_groups"],
                      "status": s.diagnostics()["status"]}
         s.close()
+        if not args.no_cpu_baseline:   # the oracle on one core, on the same mesh
+            steps = 20 if name == "flat2d" else 4
+            rate, secs, _ = oracle_rate(case, steps, warmup=1)
+            out[name]["oracle_1core"] = {"node_updates_per_s": rate, "steps": steps,
+                                         "seconds": secs}
     return out
 
 
