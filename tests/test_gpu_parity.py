@@ -76,6 +76,14 @@ def test_sphere_3d_small():
     _compare(case, 100)
 
 
+@pytest.mark.parametrize("lattice", ["D3Q19", "D3Q27"])
+def test_benchmark_mesh_cubic_sets_full_size(lattice):
+    """The bench's D3Q19 and D3Q27 lines: the full 16^3-hex sphere mesh at N = 5,
+    one step, every element-local value against the oracle."""
+    case = inputs.sphere_3d(lattice=lattice)
+    _compare(case, 1, rhs_pair_groups=1)
+
+
 def test_sphere_cap_d3q13_1000_steps():
     """The 3D case of Sec. 3.2 (sphere-cap wall at 60 degrees, D3Q13) on 18 curved
     hexes at N = 4, held to 1e-12 relative after 1000 steps."""

@@ -15,16 +15,17 @@ pytestmark = pytest.mark.gpu
 def test_continuous_batching_equals_alone():
     from paper_2609_00535_b300 import semlbm
     kinds = ["flat2d", "cylinder2d", "sphere3d", "droplet2d", "droplet3d", "flat2d"]
-    reqs = [inputs.Request(i, 0.04 * i, k, 64 if "3d" in k else 96, 4 + i % 3,
+    # arrivals 20 ms apart, each request 600 steps: several are on the GPU at once
+    reqs = [inputs.Request(i, 0.02 * i, k, 64 if "3d" in k else 96, 4 + i % 3,
                            math.radians(20 + 25 * i), 1.0, 1000 + i) for i, k in enumerate(kinds)]
-    srv = Server(hbm_budget_bytes=4 << 30, epoch_steps=20, ke_tol=0.0, max_steps=100,
+    srv = Server(hbm_budget_bytes=4 << 30, epoch_steps=20, ke_tol=0.0, max_steps=600,
                  min_steps=20, keep_state=True, workers=3)
     st = srv.run(reqs)
     summ = st.summary()
     assert summ["completed"] == len(reqs) and summ["failed"] == 0
     assert summ["max_slots"] >= 2 and summ["overlapped_admissions"] >= 1
     for req, rec in zip(reqs, st.records):
-        assert rec.steps >= 100 and rec.state is not None
+        assert rec.steps >= 600 and rec.state is not None
         case = req.case()
         s = semlbm.Solver.from_case(case)
         s.set_density(case.rho0)
