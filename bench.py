@@ -35,11 +35,11 @@ import hashlib  # noqa: E402
 METRIC = "FP64 GLL node-updates/s (3D droplet)"
 
 # DRAM traffic of one k_rhs launch from an ncu capture of the 12^3-hex
-# sphere-cap mesh at N = 5 (373,248 nodes: 82.14 MB read + 4.20 MB written, the
+# sphere-cap mesh at N = 5 (373,248 nodes: 108.96 MB read + 8.83 MB written, the
 # mean of two launches); the traffic grows with the node count, so it is scaled
 # per node.  Valid only while the kernel sources are the ones profiled.
-RHS_TRAFFIC = {"kernels.cuh": "edcb6377d1397c66", "lattice.cuh": "2210c9bd29fce6f9",
-               "bytes_per_node": (82.14e6 + 4.20e6) / 373248, "lattice": "D3Q13", "N": 5}
+RHS_TRAFFIC = {"kernels.cuh": "a0e3554c6f083886", "lattice.cuh": "1d976e7cd6cedfe1",
+               "bytes_per_node": (108.96e6 + 8.83e6) / 373248, "lattice": "D3Q13", "N": 5}
 
 
 def rhs_traffic_per_launch(lattice, N, n_local):

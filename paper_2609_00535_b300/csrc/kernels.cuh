@@ -272,6 +272,25 @@ __global__ void __launch_bounds__(cta_threads<D, NP, EPB>()) k_geom(const double
     }
 }
 
+// pair coefficients of the streaming right-hand side, stored once per node for
+// sets whose contraction costs multiplies: CJ[p][b] = (M_e S J^-1 C_rep(p))_b,
+// the same expression k_rhs would evaluate (same bits)
+template <class L>
+__global__ void k_pair_metric(const double* __restrict__ MJ, double* __restrict__ CJ, int64_t V) {
+  constexpr int D = L::D;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= V) return;
+  double J[D][D];
+  for (int b = 0; b < D; ++b)
+    for (int a = 0; a < D; ++a) J[b][a] = MJ[(b * D + a) * V + i];
+  static_for<0, L::NREP>([&](auto RR) {
+    constexpr int A = L::rep(decltype(RR)::value);
+#pragma unroll
+    for (int b = 0; b < D; ++b)
+      CJ[(int64_t)(decltype(RR)::value * D + b) * V + i] = L::template cdot<A>(J[b]);
+  });
+}
+
 // assembled mass: invMg[g] = 1 / sum over copies of M_e
 static __global__ void k_dss_mass(const int* __restrict__ off, const int* __restrict__ idx, int G,
                            const double* __restrict__ Me, double* __restrict__ invMg) {
@@ -373,6 +392,7 @@ struct View {
   double* drho;                                    // [D][V] reference gradient of rho (k_lap)
   int* flags;                                      // [0] setup, [1] non-finite
   const double *MJ, *Gm, *Me, *invMg, *Dm;        // geometry (MJ = M_e S J^-1), GLL D
+  const double* CJ;   // [NREP][D][V] (M_e S J^-1 C_rep(p))_b, sets with PAIR_METRIC
   const int *off, *idx, *wslot;                    // gather-scatter CSR, wall slots
   const double *wet, *ae;                          // wall records
   const double* wub;   // [Q][R] flux bounce-back wall-velocity coefficients (or unused)
@@ -644,11 +664,13 @@ __device__ __forceinline__ void rhs_compute(const View& v, const double* sD, con
   double vv[D];   // d_b rho - (rho / c_s^2) d_b mu, reference components
 #pragma unroll
   for (int b = 0; b < D; ++b) vv[b] = fma(-rh3, dm[b], dr[b]);
-  double J[D][D];   // M_e S J^-1
+  double J[D][D];   // M_e S J^-1 (unless the pair coefficients are stored)
+  if constexpr (!L::PAIR_METRIC) {
 #pragma unroll
-  for (int b = 0; b < D; ++b)
+    for (int b = 0; b < D; ++b)
 #pragma unroll
-    for (int a = 0; a < D; ++a) J[b][a] = __ldg(MJ + (b * D + a) * V + idx);
+      for (int a = 0; a < D; ++a) J[b][a] = __ldg(MJ + (b * D + a) * V + idx);
+  }
   const int slot = __ldg(wslot + idx);
   static_for<0, L::NREP>([&](auto RR) {
     constexpr int A = L::rep(decltype(RR)::value), B = L::opp(A);
@@ -658,8 +680,14 @@ __device__ __forceinline__ void rhs_compute(const View& v, const double* sD, con
       if (RI < pr0 || RI >= pr1) return;
     }
     double c[D];   // (M_e S J^-1 C_A)_b: M_e e_A . grad = sum_b c_b d_b
+    if constexpr (L::PAIR_METRIC) {
 #pragma unroll
-    for (int b = 0; b < D; ++b) c[b] = L::template cdot<A>(J[b]);
+      for (int b = 0; b < D; ++b)
+        c[b] = __ldg(v.CJ + (int64_t)(decltype(RR)::value * D + b) * V + idx);
+    } else {
+#pragma unroll
+      for (int b = 0; b < D; ++b) c[b] = L::template cdot<A>(J[b]);
+    }
     double dA[D], dB[D];
     grad_ref2<D, NP>(sD, ix, sg + (A - 1) * NT + lb, sg + (B - 1) * NT + lb, k, dA, dB);
     // r_A = M_e (t e_A.v - e_A.grad g_A), r_B = -M_e (t e_A.v - e_A.grad g_B), e_B = -e_A

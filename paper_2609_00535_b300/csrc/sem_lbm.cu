@@ -287,6 +287,8 @@ struct Impl {
                                                                   (int)s.E);
     k_dss_mass<<<grid_of(s.G, kDssThreads), kDssThreads, 0, s.stream>>>(s.off, s.idx, (int)s.G,
                                                                         s.Me, s.invMg);
+    if constexpr (L::PAIR_METRIC)
+      k_pair_metric<L><<<grid_of(s.V, 256), 256, 0, s.stream>>>(s.MJ, s.CJ, s.V);
   }
   static void wallsetup(sem_lbm& s) {
     if (s.R == 0) return;
@@ -461,6 +463,10 @@ size_t layout(sem_lbm& s, char* base) {
   s.Fp = c.take<double>(D * V);
   s.drho = c.take<double>(D * V);
   s.MJ = c.take<double>(D * D * V);
+  // stored pair coefficients: D3Q13 only (its contraction costs 3 fma per pair)
+  const bool pair_metric = s.lat == SEMLBM_D3Q13;
+  s.CJ = c.take<double>(pair_metric ? (Q - 1) / 2 * D * V : 0);
+  if (!pair_metric) s.CJ = nullptr;
   s.Gm = c.take<double>(D * (D + 1) / 2 * V);
   s.Me = c.take<double>(V);
   s.invMg = c.take<double>(s.G);
@@ -494,7 +500,7 @@ void fill_view(sem_lbm& s) {
   v.f = s.f; v.fs = s.fs; v.g = s.g; v.r = s.r;
   v.rho = s.rho; v.mu = s.mu; v.lapr = s.lapr; v.Fp = s.Fp; v.drho = s.drho;
   v.flags = s.flags;
-  v.MJ = s.MJ; v.Gm = s.Gm; v.Me = s.Me; v.invMg = s.invMg; v.Dm = s.Dm;
+  v.MJ = s.MJ; v.Gm = s.Gm; v.Me = s.Me; v.invMg = s.invMg; v.Dm = s.Dm; v.CJ = s.CJ;
   v.off = s.off; v.idx = s.idx; v.wslot = s.slot; v.wet = s.wet; v.ae = s.ae;
   v.R = (int)s.R; v.E = (int)s.E; v.G = (int)s.G;
   v.wub = s.wub;
@@ -536,6 +542,7 @@ size_t sem_lbm_workspace_bytes(const sem_lbm_mesh* mesh, int N, sem_lbm_lattice 
   p.theta_tag = many.data();
   if (build_maps(mesh, N, M_PI / 2, &p, h)) return 0;
   sem_lbm s{};
+  s.lat = lattice;
   s.D = mesh->dim;
   s.N = N;
   s.n = N + 1;

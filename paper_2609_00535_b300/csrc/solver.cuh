@@ -86,6 +86,7 @@ struct sem_lbm {
   size_t ws_bytes = 0;
   // device arrays
   double *f, *fs, *g, *r, *rho, *mu, *lapr, *Fp, *drho, *MJ, *Gm, *Me, *invMg, *xyz, *Dm, *wg;
+  double* CJ = nullptr;   // stored pair coefficients of the streaming kernel (D3Q13)
   int *off, *idx, *slot, *rec_elem, *rec_node, *rec_mask, *flags;
   double *wet, *ae, *rec_cos, *rec_ub, *wub;
   int* rec_tag;                         // [R][2D] wall tag per face (-1: not a wall face)

@@ -11,7 +11,9 @@ metric array holds M_e S J^-1, so the mass and the speed scale cost nothing):
                                             stored by k_lap of the same stage)
   v_b = d_b rho - (rho/c_s^2) d_b mu        1 mul + d fma
   per velocity pair, c = M_e S J^-1 C_alpha D2Q9: 0 (axis) or d adds (diagonal);
-                                            D3Q13: d fma; cubic sets: (k-1) d adds
+                                            cubic sets: (k-1) d adds; D3Q13: none
+                                            (its d fma per pair are done once per
+                                            mesh, k_pair_metric, and c is read)
   per velocity pair, t c.v                  1 mul + (d-1) fma, 1 mul
   per moving velocity                       d derivatives, d fma (t c.v - c.dg)
   wall records, per moving velocity         1 sub + 1 fma
@@ -31,18 +33,20 @@ _REP_NONZERO = {
     "D3Q27": [1] * 3 + [2] * 6 + [3] * 4,
 }
 _DIM = {"D2Q9": 2, "D3Q13": 3, "D3Q19": 3, "D3Q27": 3}
+# sets whose pair coefficients M_e S J^-1 C are stored per node (k_rhs reads
+# (Q-1)/2 x d of them instead of the d x d metric)
+_STORED_PAIRS = ("D3Q13",)
 
 
 def _pair_coeff_work(lattice, d):
-    """c_b = (J^-1 C)_b for every pair: adds for unit components, an fma for phi."""
+    """c_b = (J^-1 C)_b for every pair: adds for unit components.  D3Q13's
+    coefficients (an fma with phi each) are stored per node at setup."""
+    if lattice in _STORED_PAIRS:
+        return 0, 0
     ops = flops = 0
     for k in _REP_NONZERO[lattice]:
-        if lattice == "D3Q13":
-            ops += d          # one fma per reference direction
-            flops += 2 * d
-        else:
-            ops += (k - 1) * d
-            flops += (k - 1) * d
+        ops += (k - 1) * d
+        flops += (k - 1) * d
     return ops, flops
 
 
@@ -71,10 +75,12 @@ def rhs_work(lattice, N, n_local, n_wall_nodes):
 
 def rhs_bytes_per_node(lattice, N):
     """Minimum DRAM bytes of k_rhs per node: read g (Q-1), rho, mu, grad rho (d),
-    J^-1 (d^2), M_e, wall slot (4 B); write r (Q-1)."""
+    the metric M_e S J^-1 (d^2; or the stored pair coefficients, (Q-1)/2 x d),
+    M_e, wall slot (4 B); write r (Q-1)."""
     d = _DIM[lattice]
     Q = 2 * len(_REP_NONZERO[lattice]) + 1
-    return 8 * ((Q - 1) + 2 + d + d * d + 1 + (Q - 1)) + 4
+    metric = (Q - 1) // 2 * d if lattice in _STORED_PAIRS else d * d
+    return 8 * ((Q - 1) + 2 + d + metric + 1 + (Q - 1)) + 4
 
 
 # ---------------------------------------------------------------------------
