@@ -516,6 +516,73 @@ def angle_resolution_section(args, device):
     return out
 
 
+def angle_resolution_3d_section(args, device):
+    """Static contact angle on the sphere wall of the Sec. 3.2 box (radius 0.7)
+    against the interface width: the relaxing sphere-wall request (drop radius
+    0.13 at its equilibrium position, beta 0.1, interface 2.5 node spacings,
+    force_split 1, tau from inputs.viscous_tau) on ne^3 curved hexes at N = 4,
+    so delta / R = 0.4, 0.3 and 0.2 for ne = 6, 8 and 12.  Each drop starts
+    between the bulk densities rho_l, rho_v, and again between the densities
+    shifted by inputs.kelvin_shift for its radius ("saturated": the vapour
+    already at the density a drop of that size holds at rest, so the drop does
+    not evaporate to reach it).  Each solve runs in one batch until
+    KE_max < 1e-12 or the step budget; the angle comes from the device wetting
+    moments with the sphere-sphere lens geometry."""
+    import math
+    from paper_2609_00535_b300 import semlbm, wetting
+    angles = [float(a) for a in args.angle_study_degrees.split(",")]
+    b = semlbm.Batch(device=device)
+    live = {}
+    for saturated in (False, True):
+        for ne in (6, 8, 12):
+            for deg in angles:
+                c = inputs.relaxing_case("relaxsphere3d", ne ** 3, 4, math.radians(deg))
+                if saturated:
+                    dr = inputs.kelvin_shift(c.beta, c.kappa, c.rho_l, c.rho_v, 0.13, 3)
+                    c.rho0 = inputs.curved_cap_density(
+                        c.mesh, (0.25, 0.25, -0.7), 0.7, 0.13, math.radians(deg),
+                        c.extra["delta"], (0.0, 0.0, 1.0), c.rho_l + dr, c.rho_v + dr)
+                s = semlbm.Solver.from_case(c, device=device)
+                s.set_density(c.rho0)
+                live[b.add(s)] = (ne, c, deg, s, saturated)
+    out = []
+    done = 0
+    while live and done < args.angle_study_3d_max_steps:
+        b.step(args.angle_study_epoch)
+        done += args.angle_study_epoch
+        diag = b.diagnostics()
+        for slot in list(live):
+            ne, c, deg, s, saturated = live[slot]
+            d = diag[slot]
+            if d["status"] == 0 and d["ke_max"] >= 1e-12 and done < args.angle_study_3d_max_steps:
+                continue
+            b.remove(slot)
+            delta = c.extra["delta"]
+            row = {"mesh": "%d^3 hexes, N=4" % ne, "delta": delta, "delta_over_R": delta / 0.13,
+                   "saturated": saturated, "tau": c.tau, "theta_deg": deg, "steps": done,
+                   "ke_max": d["ke_max"], "status": d["status"],
+                   "rho_min": d["rho_min"], "rho_max": d["rho_max"]}
+            if d["status"] == 0:
+                m = s.wetting_moments(0)
+                row["volume"], row["wetted"] = m["volume"], m["wetted"]
+                try:
+                    row["measured_deg"] = wetting.contact_angle(m, 3, delta=delta, wall_radius=0.7)
+                    row["error_deg"] = row["measured_deg"] - deg
+                except ValueError as exc:       # no drop left on the wall
+                    row["error"] = str(exc)
+                try:   # independent estimate: sphere fitted to the mid-density contour
+                    row["contour_deg"] = wetting.contour_angle_on_curved_wall(
+                        c.mesh.node_xyz, s.field("rho").reshape(c.mesh.n_elem, -1), 5, 3,
+                        (0.25, 0.25, -0.7), 0.7, delta)
+                except ValueError as exc:
+                    row["contour_error"] = str(exc)
+            out.append(row)
+            s.close()
+            del live[slot]
+    b.close()
+    return out
+
+
 def lattice_section(args, device):
     """The sphere workload with the cubic velocity sets D3Q19 and D3Q27 (same mesh,
     N and parameters): node-updates/s and the k_rhs FP64 roofline of each."""
@@ -683,6 +750,8 @@ def native_arm(args):
             batched_small = batched_section(args, device, small_solves())
         lattices = None if args.no_lattices else lattice_section(args, device)
         angle_study = angle_resolution_section(args, device) if args.angle_study else None
+        angle_study_3d = (angle_resolution_3d_section(args, device)
+                          if args.angle_study_3d else None)
         configs = None if args.no_configs else config_lines_section(args, device)
         sweep = serving_c5 = None
         if not args.no_serving:
@@ -737,6 +806,7 @@ def native_arm(args):
             "angle_sweep": sweep,
             "lattices": lattices,
             "angle_resolution": angle_study,
+            "angle_resolution_3d": angle_study_3d,
             "final_diag": {"ke_max": d["ke_max"], "mass": d["mass"], "status": d["status"]},
         }
         print(json.dumps(line), flush=True)
@@ -774,6 +844,9 @@ def main():
     ap.add_argument("--lattice-steps", type=int, default=50)
     ap.add_argument("--angle-study", action="store_true",
                     help="flat-wall contact angle at three interface widths (minutes)")
+    ap.add_argument("--angle-study-3d", action="store_true",
+                    help="add the sphere-wall contact angle at four interface widths")
+    ap.add_argument("--angle-study-3d-max-steps", type=int, default=200000)
     ap.add_argument("--angle-study-degrees", default="60,90,120")
     ap.add_argument("--angle-study-epoch", type=int, default=2000)
     ap.add_argument("--angle-study-max-steps", type=int, default=600000)

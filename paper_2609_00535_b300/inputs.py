@@ -307,6 +307,20 @@ def kappa_from_width(beta, delta, rho_l, rho_v):
     return beta * delta ** 2 * (rho_l - rho_v) ** 2 / 8
 
 
+def kelvin_shift(beta, kappa, rho_l, rho_v, R, dim):
+    """Density shift of both bulk phases around a drop of radius R at rest.  The
+    Laplace pressure (dim - 1) gamma / R (gamma of Appendix A) raises the chemical
+    potential of both phases by dmu = (dim - 1) gamma / (R (rho_l - rho_v)), and the
+    double well's curvature there, d mu0 / d rho = 2 beta (rho_l - rho_v)^2 at
+    rho_v and at rho_l, turns it into the shift d rho = dmu / (d mu0 / d rho).  A
+    drop started between the unshifted densities in a closed box evaporates until
+    its vapour carries the shift: with a vapour volume V_v, a liquid mass of about
+    V_v d rho leaves the drop, which can be most of a small drop."""
+    gamma = (rho_l - rho_v) ** 3 * math.sqrt(2 * kappa * beta) / 6
+    dmu = (dim - 1) * gamma / (R * (rho_l - rho_v))
+    return dmu / (2 * beta * (rho_l - rho_v) ** 2)
+
+
 CAPILLARY_NUMBER = 0.1
 
 

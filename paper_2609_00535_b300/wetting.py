@@ -22,8 +22,14 @@ that adds pi^2 delta^2 theta / 48 to the 2D area, pi^3 delta^2 R (1 - cos theta)
 to the 3D volume, and pi^3 (delta / sin theta)^2 / 48 to the 3D wetted area (the
 contact circle, crossed at angle theta); the 2D wetted length has no correction.
 With delta > 0 these are removed by a fixed-point iteration.
+
+A second, independent estimate on curved walls fits a circle (2D) or sphere (3D)
+to the density contour halfway between the phases, away from the wall, and takes
+the angle between it and the wall (contour_angle_on_curved_wall).
 """
 import math
+
+import numpy as np
 
 
 def _bisect(fn, target, lo=1e-9, hi=math.pi - 1e-9, iters=200):
@@ -159,3 +165,51 @@ def contact_angle(moments, dim, delta=0.0, wall_radius=None):
     _check(moments["volume"], moments["wetted"])
     f = cap_angle_2d if dim == 2 else cap_angle_3d
     return math.degrees(f(moments["volume"], moments["wetted"], delta))
+
+
+def contour_points(xyz, rho, level, n, dim):
+    """Crossings of rho = level along the element-local GLL lines of every
+    element, by linear interpolation between neighbouring nodes.  xyz is
+    [E, n^dim, dim] and rho [E, n^dim] (nodes i fastest); returns [P, dim]."""
+    E = rho.shape[0]
+    R = np.asarray(rho).reshape((E,) + (n,) * dim)
+    X = np.asarray(xyz).reshape((E,) + (n,) * dim + (dim,))
+    pts = []
+    for ax in range(1, dim + 1):
+        a = np.moveaxis(R, ax, -1)
+        xa = np.moveaxis(X, ax, -2)
+        at = np.nonzero((a[..., :-1] - level) * (a[..., 1:] - level) < 0)
+        nxt = at[:-1] + (at[-1] + 1,)
+        t = (level - a[at]) / (a[nxt] - a[at])
+        pts.append(xa[at] + t[:, None] * (xa[nxt] - xa[at]))
+    return np.vstack(pts)
+
+
+def fit_sphere(p):
+    """Least-squares circle (2D) or sphere (3D) through the points p [P, dim]:
+    |x|^2 = 2 c.x + (R^2 - |c|^2) is linear in c and the constant.  Returns
+    (centre, radius)."""
+    A = np.c_[2 * p, np.ones(len(p))]
+    sol = np.linalg.lstsq(A, (p ** 2).sum(1), rcond=None)[0]
+    c = sol[:-1]
+    return c, math.sqrt(sol[-1] + c @ c)
+
+
+def contour_angle_on_curved_wall(xyz, rho, n, dim, wall_center, Rw, exclude, level=None):
+    """Contact angle (degrees) of a drop on a circular (2D) or spherical (3D) wall
+    of radius Rw from the contour rho = level (default: halfway between the
+    smallest and largest density): the points farther than Rw + exclude from the
+    wall centre are fitted with a circle/sphere of centre c and radius Rd, and
+    cos(theta) = (Rw^2 + Rd^2 - |c - wall_center|^2) / (2 Rw Rd)."""
+    rho = np.asarray(rho)
+    if level is None:
+        level = 0.5 * (float(rho.min()) + float(rho.max()))
+    p = contour_points(xyz, rho, level, n, dim)
+    wc = np.asarray(wall_center, dtype=np.float64)
+    p = p[np.linalg.norm(p - wc, axis=1) > Rw + exclude]
+    if len(p) < dim + 1:
+        raise ValueError("no drop contour away from the wall")
+    c, Rd = fit_sphere(p)
+    d2 = float((c - wc) @ (c - wc))
+    return math.degrees(math.acos(max(-1.0, min(1.0, (Rw * Rw + Rd * Rd - d2) / (2 * Rw * Rd)))))
+

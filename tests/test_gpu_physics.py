@@ -5,7 +5,9 @@
   settle below the prescribed angle (108 for 120 degrees) or lift off at 150,
   so those angles are not asserted,
 * contact angle on a circular cylinder from the circle-circle geometry
-  cos(theta) = (R_c^2 + R_d^2 - d^2) / (2 R_c R_d) (Sec. 3.2),
+  cos(theta) = (R_c^2 + R_d^2 - d^2) / (2 R_c R_d) (Sec. 3.2), and on the
+  sphere wall of the Sec. 3.2 box from the sphere-sphere geometry, with the
+  vapour started at the Kelvin-shifted density of the drop's radius,
 * Laplace's law gamma / R for drops of several radii (Appendix A gamma), and
   the drop's residual kinetic energy reaching the paper's isolated-drop level
   (~1e-30, Sec. 3.3) in a closed box with neutral walls,
@@ -214,21 +216,48 @@ def test_flat_wall_contact_angle_3d(deg):
     assert abs(th - deg) < 4.0, (deg, th)
 
 
-@pytest.mark.parametrize("deg", [60, 90, 120])
-def test_sphere_wall_contact_angle_3d(deg):
-    """A drop on the sphere-cap bottom of Sec. 3.2 (wall sphere of radius 0.7
-    under the 0.5 x 0.5 x 0.25 box, D3Q13), started at its equilibrium position
-    on the sphere, keeps the prescribed angle; measured from the device's
-    wetting moments with the sphere-sphere lens geometry."""
-    m = inputs.sphere_cap_box(5, (8, 8, 6))
-    th0 = math.radians(deg)
-    c = make_case("sph", m, "D3Q13", 0.01, 0.035, 1.0, th0,
-                  rho0=inputs.curved_cap_density(m, (0.25, 0.25, -0.7), 0.7, 0.13, th0, 0.035,
-                                                 (0.0, 0.0, 1.0)))
-    rho, d, w = _run(c, 12000, moments=True)
-    assert d["status"] == 0 and d["ke_max"] < 1e-6, d
-    th = wetting.contact_angle(w, 3, delta=0.035, wall_radius=0.7)
-    assert abs(th - deg) < 5.0, (deg, th)         # 60 degrees measures 55.5 (delta/R ~ 0.27)
+def test_sphere_wall_contact_angle_3d():
+    """Drops on the sphere-cap bottom of Sec. 3.2 (wall sphere of radius 0.7
+    under the 0.5 x 0.5 x 0.25 box, D3Q13) at 60, 90 and 120 degrees: the relaxing
+    sphere-wall request on 8^3 curved hexes at N = 4 (drop radius 0.13, interface
+    2.5 node spacings, delta / R = 0.3), started at its equilibrium position with
+    both bulk densities raised by the Kelvin shift of its radius (otherwise the
+    closed box's vapour takes most of a 60-degree drop before it comes to rest).
+    After 5e4 steps in one batch every drop is at rest, has kept its volume, and a
+    sphere fitted to its mid-density contour meets the wall within 3.5 degrees of
+    the prescribed angle.  The device moments agree within 3.5 degrees at 90 and
+    120; at 60 the cap is only ~2.4 interface widths high and their diffuse-interface
+    correction leaves 7 degrees (the error of both falls with delta / R)."""
+    from paper_2609_00535_b300 import semlbm
+    b = semlbm.Batch()
+    runs = {}
+    for deg in (60, 90, 120):
+        th0 = math.radians(deg)
+        c = inputs.relaxing_case("relaxsphere3d", 8 ** 3, 4, th0)
+        dr = inputs.kelvin_shift(c.beta, c.kappa, c.rho_l, c.rho_v, 0.13, 3)
+        c.rho0 = inputs.curved_cap_density(c.mesh, (0.25, 0.25, -0.7), 0.7, 0.13, th0,
+                                           c.extra["delta"], (0.0, 0.0, 1.0),
+                                           c.rho_l + dr, c.rho_v + dr)
+        s = semlbm.Solver.from_case(c)
+        s.set_density(c.rho0)
+        runs[b.add(s)] = (deg, c, s)
+    b.step(50000)
+    d = b.diagnostics()
+    for slot, (deg, c, s) in runs.items():
+        assert d[slot]["status"] == 0 and d[slot]["ke_max"] < 1e-11, (deg, d[slot])
+        delta = c.extra["delta"]
+        w = s.wetting_moments(0)
+        vol0 = wetting.curved_cap(0.7, 0.13, math.radians(deg), 3)[0]
+        assert abs(w["volume"] / vol0 - 1) < 0.06, (deg, w, vol0)
+        th_c = wetting.contour_angle_on_curved_wall(
+            c.mesh.node_xyz, s.field("rho").reshape(c.mesh.n_elem, -1), 5, 3,
+            (0.25, 0.25, -0.7), 0.7, delta)
+        th_m = wetting.contact_angle(w, 3, delta=delta, wall_radius=0.7)
+        assert abs(th_c - deg) < 3.5, (deg, th_c, th_m)
+        assert abs(th_m - deg) < (8.0 if deg == 60 else 3.5), (deg, th_c, th_m)
+    b.close()
+    for _, _, s in runs.values():
+        s.close()
 
 
 def test_flat_wall_wetting_residual():

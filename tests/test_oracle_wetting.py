@@ -155,3 +155,31 @@ def test_diffuse_caps_on_a_sphere(deg):
                                      (0.0, 0.0, 1.0))
     w = _moments(m, "D3Q13", rho0)
     assert wetting.contact_angle(w, 3, delta=0.04, wall_radius=0.7) == pytest.approx(deg, abs=2.5)
+
+
+@pytest.mark.parametrize("deg", [60, 90, 120])
+def test_contour_sphere_fit_on_a_sphere(deg):
+    """The contour estimate recovers the angle of the equilibrium-cap initial
+    density on the sphere wall of Sec. 3.2 (the tanh profile is centred on the
+    drop's sphere, so the mid-density contour is that sphere up to the
+    interpolation between nodes)."""
+    m = inputs.sphere_cap_box(5, (8, 8, 6))
+    rho0 = inputs.curved_cap_density(m, (0.25, 0.25, -0.7), 0.7, 0.14, math.radians(deg), 0.04,
+                                     (0.0, 0.0, 1.0))
+    th = wetting.contour_angle_on_curved_wall(m.node_xyz, rho0.reshape(m.n_elem, -1), 6, 3,
+                                              (0.25, 0.25, -0.7), 0.7, 0.04, level=0.55)
+    assert th == pytest.approx(deg, abs=0.5)
+
+
+def test_contour_circle_fit_on_a_cylinder():
+    """The same estimate in 2D, on the cylinder cap, and the least-squares fit
+    itself on exact points of a circle."""
+    t = np.linspace(0.3, 2.5, 40)
+    c, R = wetting.fit_sphere(np.c_[0.2 + 0.7 * np.cos(t), -0.1 + 0.7 * np.sin(t)])
+    assert np.allclose(c, [0.2, -0.1], atol=1e-12) and R == pytest.approx(0.7, abs=1e-12)
+    m = inputs.cylinder_ogrid(8, n_theta=48, n_r=10, Rc=0.15)
+    rho0 = inputs.cylinder_cap_density(m, (0.5, 0.5), 0.15, 0.15, math.radians(60), 0.06)
+    th = wetting.contour_angle_on_curved_wall(m.node_xyz, rho0.reshape(m.n_elem, -1), 9, 2,
+                                              (0.5, 0.5), 0.15, 0.06, level=0.55)
+    assert th == pytest.approx(60, abs=0.5)
+
