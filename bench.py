@@ -35,11 +35,11 @@ import hashlib  # noqa: E402
 METRIC = "FP64 GLL node-updates/s (3D droplet)"
 
 # DRAM traffic of one k_rhs launch from an ncu capture of the 12^3-hex
-# sphere-cap mesh at N = 5 (373,248 nodes: 108.96 MB read + 8.83 MB written, the
+# sphere-cap mesh at N = 5 (373,248 nodes: 109.01 MB read + 8.78 MB written, the
 # mean of two launches); the traffic grows with the node count, so it is scaled
 # per node.  Valid only while the kernel sources are the ones profiled.
-RHS_TRAFFIC = {"kernels.cuh": "a0e3554c6f083886", "lattice.cuh": "1d976e7cd6cedfe1",
-               "bytes_per_node": (108.96e6 + 8.83e6) / 373248, "lattice": "D3Q13", "N": 5}
+RHS_TRAFFIC = {"kernels.cuh": "f7e5f26e7ac45be1", "lattice.cuh": "1d976e7cd6cedfe1",
+               "bytes_per_node": (109.01e6 + 8.78e6) / 373248, "lattice": "D3Q13", "N": 5}
 
 
 def rhs_traffic_per_launch(lattice, N, n_local):
@@ -696,36 +696,47 @@ def native_arm(args):
 
     # end to end through the public API with host buffers: every step's input
     # state is uploaded from pinned host memory, the step advances it and its
-    # diagnostics are read back to the host.  The upload of step k+1's input
-    # (a copy stream, into the other of two device staging buffers) overlaps
-    # step k's compute; set_state then takes it device to device.
-    Q, V = info["Q"], info["n_local"]
-    host = torch.empty(Q * V, dtype=torch.float64).pin_memory()
-    st, _ = solver.get_state()
-    host.copy_(torch.from_numpy(st.reshape(-1)))
-    stage = [torch.empty(Q * V, dtype=torch.float64, device=device) for _ in range(2)]
-    copy = torch.cuda.Stream(device=device)
+    # diagnostics are read back to the host.  The input is the compact state,
+    # one value per global node and velocity (sem_lbm_set_state_global): the
+    # copies of a shared node are equal, so it holds the whole state in G/V of
+    # the element-local bytes.  The upload of step k+1's input (a copy stream,
+    # into the other of two device staging buffers) overlaps step k's compute;
+    # set_state_global then scatters it to the element copies on the device.
+    # The same loop with the element-local state (set_state) is reported too.
+    Q, V, G = info["Q"], info["n_local"], info["n_global"]
     e2e_steps = max(1, min(args.steps, 100))
 
-    def e2e_run(n):
-        with torch.cuda.stream(copy):
-            stage[0].copy_(host, non_blocking=True)
-        for k in range(n):
-            with torch.cuda.stream(copy):
-                solver.set_state(stage[k % 2], 0)          # waits for this input's upload
-                if k + 1 < n:                              # buffer last read by step k-1
-                    stage[(k + 1) % 2].copy_(host, non_blocking=True)
-            solver.step(1)
-            solver.diagnostics()                           # device-to-host read, synchronises
+    def e2e_measure(n_values, set_fn, state):
+        host = torch.empty(n_values, dtype=torch.float64).pin_memory()
+        host.copy_(torch.from_numpy(state.reshape(-1)))
+        stage = [torch.empty(n_values, dtype=torch.float64, device=device) for _ in range(2)]
+        copy = torch.cuda.Stream(device=device)
 
-    e2e_run(2)
-    barrier()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    e2e_run(e2e_steps)
-    torch.cuda.synchronize()
-    e2e_s = max_over_ranks(time.perf_counter() - t0, device="cuda")
+        def run(n):
+            with torch.cuda.stream(copy):
+                stage[0].copy_(host, non_blocking=True)
+            for k in range(n):
+                with torch.cuda.stream(copy):
+                    set_fn(stage[k % 2], 0)                    # waits for this input's upload
+                    if k + 1 < n:                              # buffer last read by step k-1
+                        stage[(k + 1) % 2].copy_(host, non_blocking=True)
+                solver.step(1)
+                solver.diagnostics()                           # device-to-host read, synchronises
+
+        run(2)
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        run(e2e_steps)
+        torch.cuda.synchronize()
+        return max_over_ranks(time.perf_counter() - t0, device="cuda")
+
+    st_local, _ = solver.get_state()
+    st_global, _ = solver.get_state_global()
+    e2e_s = e2e_measure(Q * G, solver.set_state_global, st_global)
     e2e_value = V * e2e_steps * ws / e2e_s
+    e2e_local_s = e2e_measure(Q * V, solver.set_state, st_local)
+    e2e_local_value = V * e2e_steps * ws / e2e_local_s
 
     line = None
     if rank == 0:
@@ -794,8 +805,13 @@ def native_arm(args):
                              "note": "the same K steps issued kernel by kernel with a CUDA event "
                                      "after each (source of the roofline and the kernel shares)"},
             "clocks": clk,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": Q * V * 8,
-                    "d2h_bytes_per_step": 80, "steps": e2e_steps},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": Q * G * 8,
+                    "d2h_bytes_per_step": 80, "steps": e2e_steps,
+                    "input": "compact state on the global nodes (sem_lbm_set_state_global)"},
+            "e2e_element_local": {"value": e2e_local_value, "unit": UNIT,
+                                  "h2d_bytes_per_step": Q * V * 8, "d2h_bytes_per_step": 80,
+                                  "steps": e2e_steps,
+                                  "input": "element-local state (sem_lbm_set_state)"},
             "cpu_baseline": cpu,
             "cpu_baseline_1core": cpu1,
             "configs": configs,

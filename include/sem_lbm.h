@@ -215,6 +215,27 @@ int sem_lbm_get_field(sem_lbm_t* s, int which, double* dst, int dst_on_device);
 int sem_lbm_get_state(sem_lbm_t* s, double* fbar, int on_device, int64_t* step);
 int sem_lbm_set_state(sem_lbm_t* s, const double* fbar, int on_device, int64_t step);
 
+/* Compact checkpoint: fbar on the mesh's global nodes, [Q][G] with
+ * G = sem_lbm_info_t.n_global, one value per node instead of one per element
+ * copy.  The copies of a shared node are equal after every step (the direct
+ * stiffness summation of Sec. 2.2 writes one value to all of them), so the
+ * compact state carries the whole state in G/V of the bytes (0.6 on hex meshes
+ * at N = 5).  Nodes are in the library's node-group order:
+ * sem_lbm_get_global_nodes gives, for each, the element-local index (into
+ * [E][n^d]) of its first copy, so mesh.global_id[first_copy[g]] names node g.
+ *   get: reads each node's first copy into fbar_g (device memory when on_device,
+ *        else host memory; a host copy synchronises the stream).  Errors:
+ *        SEMLBM_EINVAL (NULL argument, state not set), SEMLBM_ECUDA.
+ *   set: writes value [q][g] to every copy of node g, recomputes rho and sets
+ *        the step counter; a host source is copied (and the stream synchronised)
+ *        before the call returns, a device source is read in stream order on the
+ *        solver's stream.  The library keeps no pointer to either buffer.
+ *        Errors: SEMLBM_EINVAL (NULL argument), SEMLBM_ECUDA.
+ *   get_global_nodes: fills first_copy[G] (host memory, caller-owned). */
+int sem_lbm_get_state_global(sem_lbm_t* s, double* fbar_g, int on_device, int64_t* step);
+int sem_lbm_set_state_global(sem_lbm_t* s, const double* fbar_g, int on_device, int64_t step);
+int sem_lbm_get_global_nodes(const sem_lbm_t* s, int64_t* first_copy);
+
 int sem_lbm_get_info(const sem_lbm_t* s, sem_lbm_info_t* out);
 
 /* Per-kernel device timing, for measurement.  While enabled, sem_lbm_step

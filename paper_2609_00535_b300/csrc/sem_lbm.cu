@@ -86,7 +86,7 @@ void gll_tables(int N, std::vector<double>& x, std::vector<double>& w, std::vect
 size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
 
 struct HostMaps {
-  std::vector<int> off, idx;          // gather-scatter CSR (groups by first copy)
+  std::vector<int> off, idx;          // gather-scatter CSR (group order: see build_maps)
   std::vector<int> slot;              // [V] wall record or -1
   std::vector<int> rec_elem, rec_node, rec_mask;
   std::vector<double> rec_cos;        // [R][2D]
@@ -350,13 +350,13 @@ struct Impl {
   }
   static void diag(sem_lbm& s) {
     k_diag<L><<<s.diag_blocks, 256, 0, s.stream>>>(s.f, s.Me, s.parts, s.V);
-    k_diag_final<<<1, 32, 0, s.stream>>>(s.parts, s.diag_blocks, s.dout);
+    k_diag_final<<<1, kCombineThreads, 0, s.stream>>>(s.parts, s.diag_blocks, s.dout);
   }
   static void wet(sem_lbm& s, int tag, double rv, double rl) {
     k_wet<L><<<s.diag_blocks, 256, 0, s.stream>>>(
         s.f, s.Me, s.xyz, s.rec_elem, s.rec_node, s.rec_mask, s.rec_tag, s.wsf, (int)s.R, tag,
         (int)s.NL, rv, 1.0 / (rl - rv), s.wparts, s.V);
-    k_wet_final<<<1, 32, 0, s.stream>>>(s.wparts, s.diag_blocks, s.wout);
+    k_wet_final<<<1, kCombineThreads, 0, s.stream>>>(s.wparts, s.diag_blocks, s.wout);
   }
   static void init(sem_lbm& s, const double* rho_in) {
     k_init<L><<<grid_of(s.V, 256), 256, 0, s.stream>>>(rho_in, s.f, s.rho, s.V);
@@ -536,6 +536,34 @@ int host_copy_in(sem_lbm* s, void* dst, const void* src, size_t bytes, int src_o
   return 0;
 }
 
+// compact state: fbar on the global nodes, [Q][G] in node-group order, to and
+// from the element-local copies [Q][V]; one thread per node group.  The
+// scatter also writes rho at every copy, summed over q in the order the
+// density kernel uses (the same bits)
+__global__ void k_scatter_global(const int* __restrict__ off, const int* __restrict__ idx, int G,
+                                 int Q, int64_t V, const double* __restrict__ src,
+                                 double* __restrict__ dst, double* __restrict__ rho) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= G) return;
+  const int j0 = off[g], j1 = off[g + 1];
+  double rs = 0.0;
+  for (int q = 0; q < Q; ++q) {
+    const double val = src[(int64_t)q * G + g];
+    rs += val;
+    for (int j = j0; j < j1; ++j) dst[q * V + idx[j]] = val;
+  }
+  for (int j = j0; j < j1; ++j) rho[idx[j]] = rs;
+}
+
+__global__ void k_gather_global(const int* __restrict__ off, const int* __restrict__ idx, int G,
+                                int Q, int64_t V, const double* __restrict__ src,
+                                double* __restrict__ dst) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= G) return;
+  const int i0 = idx[off[g]];   // the first copy (all copies are equal)
+  for (int q = 0; q < Q; ++q) dst[(int64_t)q * G + g] = src[q * V + i0];
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -595,6 +623,8 @@ int sem_lbm_create(const sem_lbm_mesh* mesh, int N, sem_lbm_lattice lattice, dou
   s->E = mesh->n_elem;
   s->V = s->E * s->NL;
   s->G = h.G;
+  s->first_copy.resize(h.G);
+  for (int64_t g = 0; g < h.G; ++g) s->first_copy[g] = h.idx[h.off[g]];
   s->R = (int64_t)h.rec_elem.size();
   s->moving = h.moving;
   s->beta = beta;
@@ -705,6 +735,47 @@ int sem_lbm_set_state(sem_lbm_t* s, const double* fbar, int on_device, int64_t s
   CUDA_TRY(cudaGetLastError());
   s->state_ready = true;
   s->step = step;
+  return 0;
+}
+
+int sem_lbm_set_state_global(sem_lbm_t* s, const double* fbar_g, int on_device, int64_t step) {
+  if (!s || !fbar_g) return fail(SEMLBM_EINVAL, "NULL argument");
+  DeviceGuard dg(s->device);
+  const double* src = fbar_g;
+  if (!on_device) {   // staged in the stage-state array (overwritten by the next step anyway)
+    if (int rc = host_copy_in(s, s->g, fbar_g, sizeof(double) * s->Q * s->G, 0)) return rc;
+    src = s->g;
+  }
+  k_scatter_global<<<grid_of(s->G, 256), 256, 0, s->stream>>>(s->off, s->idx, (int)s->G, s->Q,
+                                                              s->V, src, s->f, s->rho);
+  CUDA_TRY(cudaGetLastError());
+  s->state_ready = true;
+  s->step = step;
+  return 0;
+}
+
+int sem_lbm_get_state_global(sem_lbm_t* s, double* fbar_g, int on_device, int64_t* step) {
+  if (!s || !fbar_g) return fail(SEMLBM_EINVAL, "NULL argument");
+  if (!s->state_ready) return fail(SEMLBM_EINVAL, "state not set");
+  DeviceGuard dg(s->device);
+  // a host destination is staged in the stage-state array, which only the
+  // step reads, after writing it
+  double* dst = on_device ? fbar_g : s->g;
+  k_gather_global<<<grid_of(s->G, 256), 256, 0, s->stream>>>(s->off, s->idx, (int)s->G, s->Q,
+                                                             s->V, s->f, dst);
+  CUDA_TRY(cudaGetLastError());
+  if (!on_device) {
+    CUDA_TRY(cudaMemcpyAsync(fbar_g, dst, sizeof(double) * s->Q * s->G, cudaMemcpyDeviceToHost,
+                             s->stream));
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+  }
+  if (step) *step = s->step;
+  return 0;
+}
+
+int sem_lbm_get_global_nodes(const sem_lbm_t* s, int64_t* first_copy) {
+  if (!s || !first_copy) return fail(SEMLBM_EINVAL, "NULL argument");
+  for (int64_t g = 0; g < s->G; ++g) first_copy[g] = s->first_copy[g];
   return 0;
 }
 

@@ -106,6 +106,7 @@ struct sem_lbm {
   bool graph_pdl = false;               // the captured step has programmatic edges
   sem_lbm_batch* batch = nullptr;     // set while a batch steps this solver
   cudaStream_t home_stream = nullptr; // the solver's own stream while it is in a batch
+  std::vector<int> first_copy;   // [G] element-local index of each node group's first copy
   std::vector<cudaEvent_t> ev;   // event pool; ev[0..nev) recorded since the last read
   std::vector<int> ev_cls;       // class of the kernel that ends at ev[i] (i >= 1)
   size_t nev = 0;

@@ -23,6 +23,7 @@ ERRORS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENONFINITE", -5
 
 EXPORTED = ["sem_lbm_workspace_bytes", "sem_lbm_create", "sem_lbm_set_density", "sem_lbm_step",
             "sem_lbm_diagnostics", "sem_lbm_wetting_moments", "sem_lbm_get_field", "sem_lbm_get_state", "sem_lbm_set_state",
+            "sem_lbm_get_state_global", "sem_lbm_set_state_global", "sem_lbm_get_global_nodes",
             "sem_lbm_get_info", "sem_lbm_destroy", "sem_lbm_last_error", "sem_lbm_profile",
             "sem_lbm_profile_read", "sem_lbm_chemical_potential_noalloc",
             "sem_lbm_batch_create", "sem_lbm_batch_add", "sem_lbm_batch_remove",
@@ -120,6 +121,9 @@ def load():
     L.sem_lbm_get_field.argtypes = [P, I, P, I]
     L.sem_lbm_get_state.argtypes = [P, P, I, ctypes.POINTER(I64)]
     L.sem_lbm_set_state.argtypes = [P, P, I, I64]
+    L.sem_lbm_get_state_global.argtypes = [P, P, I, ctypes.POINTER(I64)]
+    L.sem_lbm_set_state_global.argtypes = [P, P, I, I64]
+    L.sem_lbm_get_global_nodes.argtypes = [P, P]
     L.sem_lbm_get_info.argtypes = [P, ctypes.POINTER(InfoC)]
     L.sem_lbm_destroy.argtypes = [P]
     L.sem_lbm_destroy.restype = None
@@ -146,7 +150,8 @@ def load():
         getattr(L, name).restype = I
     for name in ("sem_lbm_set_density", "sem_lbm_step", "sem_lbm_diagnostics", "sem_lbm_get_field",
                  "sem_lbm_get_state", "sem_lbm_set_state", "sem_lbm_get_info", "sem_lbm_profile",
-                 "sem_lbm_profile_read"):
+                 "sem_lbm_profile_read", "sem_lbm_get_state_global", "sem_lbm_set_state_global",
+                 "sem_lbm_get_global_nodes"):
         getattr(L, name).restype = I
     _lib = L
     return L
@@ -264,6 +269,48 @@ class Solver:
             a = np.ascontiguousarray(fbar, dtype=np.float64).reshape(-1)
             assert a.size == self.Q * self.V
             check(load().sem_lbm_set_state(self.h, _ptr(a), 0, step))
+
+    def set_state_global(self, fbar_g, step=0):
+        """Compact state [Q, G] on the global nodes (sem_lbm_set_state_global), in
+        the order of global_nodes(); a CUDA tensor, a host tensor (pinned for
+        full-speed copies) or a numpy array."""
+        import torch
+        n = self.Q * self.info["n_global"]
+        if isinstance(fbar_g, torch.Tensor):
+            assert fbar_g.dtype == torch.float64 and fbar_g.is_contiguous() and fbar_g.numel() == n
+            if fbar_g.is_cuda:
+                self.stream.wait_stream(torch.cuda.current_stream(fbar_g.device))
+                check(load().sem_lbm_set_state_global(self.h, ctypes.c_void_p(fbar_g.data_ptr()),
+                                                      1, step))
+            else:
+                check(load().sem_lbm_set_state_global(self.h, ctypes.c_void_p(fbar_g.data_ptr()),
+                                                      0, step))
+        else:
+            a = np.ascontiguousarray(fbar_g, dtype=np.float64).reshape(-1)
+            assert a.size == n
+            check(load().sem_lbm_set_state_global(self.h, _ptr(a), 0, step))
+
+    def get_state_global(self, out=None):
+        """(fbar on the global nodes [Q, G], step); into a CUDA tensor when out is given."""
+        step = ctypes.c_int64()
+        if out is not None:
+            import torch
+            assert isinstance(out, torch.Tensor) and out.dtype == torch.float64 and out.is_cuda
+            assert out.is_contiguous() and out.numel() == self.Q * self.info["n_global"]
+            check(load().sem_lbm_get_state_global(self.h, ctypes.c_void_p(out.data_ptr()), 1,
+                                                  ctypes.byref(step)))
+            torch.cuda.current_stream(out.device).wait_stream(self.stream)
+            return out, step.value
+        a = np.empty((self.Q, self.info["n_global"]), dtype=np.float64)
+        check(load().sem_lbm_get_state_global(self.h, _ptr(a), 0, ctypes.byref(step)))
+        return a, step.value
+
+    def global_nodes(self):
+        """Element-local index of each global node's first copy, [G] int64: node g
+        of the compact state is mesh.global_id[global_nodes()[g]]."""
+        a = np.empty(self.info["n_global"], dtype=np.int64)
+        check(load().sem_lbm_get_global_nodes(self.h, _ptr(a)))
+        return a
 
     def step(self, n=1):
         check(load().sem_lbm_step(self.h, int(n)))

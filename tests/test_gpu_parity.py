@@ -181,6 +181,45 @@ def test_checkpoint_restart_is_bitwise():
 
 
 @pytest.mark.parametrize("kind", ["flat2d", "sphere3d"])
+def test_compact_checkpoint_on_global_nodes(kind):
+    """The compact state (one value per global node, sem_lbm_get/set_state_global)
+    holds the whole state: every copy of a node equals its node's value, and a
+    solver restarted from it, through host or device memory, steps to the same
+    bits as the original.  global_nodes() names each node's first copy: its
+    global id is the mesh's id there, and the ids are distinct."""
+    import torch
+    case = inputs.flat_wall_2d(N=4, ne=(4, 4)) if kind == "flat2d" else \
+        inputs.sphere_3d(N=5, ne=(4, 4, 3))
+    a = _solver(case)
+    a.step(30)
+    fg, k = a.get_state_global()
+    fl, _ = a.get_state()
+    first = a.global_nodes()
+    gid = np.asarray(case.mesh.global_id).reshape(-1)
+    assert len(np.unique(gid[first])) == len(first) == a.info["n_global"]
+    # every copy of node g equals fg[:, g]
+    node_of = np.empty(len(gid), dtype=np.int64)
+    order = np.argsort(gid[first])
+    node_of[:] = order[np.searchsorted(gid[first][order], gid)]
+    assert np.array_equal(fl, fg[:, node_of])
+    a.step(20)
+    fa, _ = a.get_state()
+    b = _solver(case)                               # from host memory
+    b.set_state_global(fg, k)
+    b.step(20)
+    fb, kb = b.get_state()
+    assert kb == 50 and np.array_equal(fa, fb)
+    c = _solver(case)                               # from device memory
+    dev = torch.from_numpy(fg).cuda()
+    c.set_state_global(dev, k)
+    out = torch.empty_like(dev)
+    assert np.array_equal(c.get_state_global(out)[0].cpu().numpy(), fg)
+    c.step(20)
+    assert np.array_equal(c.get_state()[0], fa)
+    a.close(); b.close(); c.close()
+
+
+@pytest.mark.parametrize("kind", ["flat2d", "sphere3d"])
 def test_graph_with_programmatic_launches_equals_plain_launches(kind):
     """A step replayed from the captured graph, whose kernels are programmatic
     dependent launches (each may start while its predecessor finishes), gives the
