@@ -64,6 +64,13 @@ def test_laplace_law_closed_box():
     ratio = (p0(rin) - p0(rout)) / (s.p.surface_tension() / math.sqrt(area / math.pi))
     assert s.diagnostics(f)["ke_max"] < 1e-6
     assert abs(ratio - 1) < 0.02, ratio
+    # both phases sit above their bulk densities by the Kelvin shift of the drop's
+    # radius (first order in gamma / R; the second-order terms of the double well
+    # move the vapour up and the liquid down by ~7 % of it)
+    dr = inputs.kelvin_shift(c.beta, c.kappa, c.rho_l, c.rho_v, math.sqrt(area / math.pi), 2)
+    assert abs((rout - c.rho_v) / dr - 1) < 0.15 and abs((rin - c.rho_l) / dr - 1) < 0.15, \
+        (dr, rout - c.rho_v, rin - c.rho_l)
+    assert abs(0.5 * (rout - c.rho_v + rin - c.rho_l) / dr - 1) < 0.05
 
 
 def test_static_contact_angle_60_degrees():
