@@ -73,6 +73,23 @@ def test_host_validation_errors():
     assert rc == -1 and "face_kind" in msg
 
 
+def test_null_arguments_are_rejected_on_the_host():
+    """Entry points given a NULL solver or buffer return SEMLBM_EINVAL (-1) and a
+    message before touching a device."""
+    import ctypes
+    L = semlbm.load()
+    buf = (ctypes.c_double * 4)()
+    step = ctypes.c_int64()
+    ids = (ctypes.c_int64 * 4)()
+    assert L.sem_lbm_get_state_global(None, buf, 0, ctypes.byref(step)) == -1
+    assert L.sem_lbm_set_state_global(None, buf, 0, 0) == -1
+    assert L.sem_lbm_get_global_nodes(None, ids) == -1
+    assert L.sem_lbm_get_state(None, buf, 0, ctypes.byref(step)) == -1
+    assert L.sem_lbm_set_state(None, buf, 0, 0) == -1
+    assert L.sem_lbm_step(None, 1) == -1
+    assert b"NULL" in L.sem_lbm_last_error()
+
+
 def test_workspace_bytes_is_host_only_and_scales():
     b1 = semlbm.workspace_bytes(inputs.box((2, 2), (0, 0), (1, 1), 4), 4, "D2Q9")
     b2 = semlbm.workspace_bytes(inputs.box((4, 4), (0, 0), (1, 1), 4), 4, "D2Q9")
