@@ -233,11 +233,8 @@ def test_sphere_wall_contact_angle_3d():
     runs = {}
     for deg in (60, 90, 120):
         th0 = math.radians(deg)
-        c = inputs.relaxing_case("relaxsphere3d", 8 ** 3, 4, th0)
-        dr = inputs.kelvin_shift(c.beta, c.kappa, c.rho_l, c.rho_v, 0.13, 3)
-        c.rho0 = inputs.curved_cap_density(c.mesh, (0.25, 0.25, -0.7), 0.7, 0.13, th0,
-                                           c.extra["delta"], (0.0, 0.0, 1.0),
-                                           c.rho_l + dr, c.rho_v + dr)
+        c = inputs.relaxing_case("relaxsphere3d", 8 ** 3, 4, th0, saturate=True)
+        assert c.extra["kelvin_shift"] > 0
         s = semlbm.Solver.from_case(c)
         s.set_density(c.rho0)
         runs[b.add(s)] = (deg, c, s)

@@ -153,3 +153,23 @@ def test_relaxing_request_stream():
     assert inputs.viscous_tau(0.01, 1.0, steps=1e4) == pytest.approx(3.0)
     assert inputs.viscous_tau(0.1, 1.0) == 1.0
     assert inputs.viscous_tau(1e-3, 1.0) == 10.0          # capped
+
+
+def test_kelvin_shifted_starts():
+    """Saturated starts put both bulk phases at the Kelvin shift of the drop's
+    radius: the equilibrium cap's circle for the flat-wall drop, the drop radius
+    for the relaxing kinds."""
+    import math
+    c0 = inputs.cap_on_wall_2d(math.radians(60))
+    c1 = inputs.cap_on_wall_2d(math.radians(60), saturate=True)
+    R = inputs.cap_radius(0.5 * math.pi * 0.25 ** 2, math.radians(60))
+    dr = inputs.kelvin_shift(c1.beta, c1.kappa, c1.rho_l, c1.rho_v, R, 2)
+    assert dr > 0
+    assert np.allclose(c1.rho0 - dr, c0.rho0, atol=1e-14)
+    c = inputs.relaxing_case("relaxsphere3d", 27, 4, math.radians(90), saturate=True)
+    assert c.extra["kelvin_shift"] == pytest.approx(
+        inputs.kelvin_shift(c.beta, c.kappa, c.rho_l, c.rho_v, 0.13, 3))
+    assert inputs.relaxing_case("relaxsphere3d", 27, 4, math.radians(90)).extra["kelvin_shift"] == 0
+    req = inputs.angle_sweep_stream(n=2)[0]
+    assert req.saturate and req.case().rho0.min() > req.case().rho_v + 1e-3
+
