@@ -249,7 +249,7 @@ int refresh_group(sem_lbm_batch* b, BatchGroup* g) {
     CUDA_TRY(cudaMemcpyAsync(g->d_node, g->h_node.data(), g->h_node.size() * sizeof(WorkItem),
                              cudaMemcpyHostToDevice, st));
   CUDA_TRY(cudaMemcpyAsync(g->d_counts, g->h_counts, 2 * sizeof(int), cudaMemcpyHostToDevice, st));
-  // the host vectors are staged by the driver (pageable), but keep ordering simple:
+  // the host vectors are pageable (the CUDA runtime stages them), but keep ordering simple:
   CUDA_TRY(cudaStreamSynchronize(st));
   return 0;
 }
