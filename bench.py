@@ -35,11 +35,11 @@ import hashlib  # noqa: E402
 METRIC = "FP64 GLL node-updates/s (3D droplet)"
 
 # DRAM traffic of one k_rhs launch from an ncu capture of the 12^3-hex
-# sphere-cap mesh at N = 5 (373,248 nodes: 109.01 MB read + 8.78 MB written, the
+# sphere-cap mesh at N = 5 (373,248 nodes: 108.96 MB read + 8.81 MB written, the
 # mean of two launches); the traffic grows with the node count, so it is scaled
 # per node.  Valid only while the kernel sources are the ones profiled.
-RHS_TRAFFIC = {"kernels.cuh": "f7e5f26e7ac45be1", "lattice.cuh": "1d976e7cd6cedfe1",
-               "bytes_per_node": (109.01e6 + 8.78e6) / 373248, "lattice": "D3Q13", "N": 5}
+RHS_TRAFFIC = {"kernels.cuh": "323819fc1b0f7d76", "lattice.cuh": "5fa95228ce9be598",
+               "bytes_per_node": (108.96e6 + 8.81e6) / 373248, "lattice": "D3Q13", "N": 5}
 
 
 def rhs_traffic_per_launch(lattice, N, n_local):

@@ -61,33 +61,36 @@ __device__ __forceinline__ void grad_ref(const double (&Dr)[D][NP], const NodeId
   if constexpr (D == 3) out[2] = dline<NP, NP * NP>(Dr[2], tile + k - ix.i[2] * NP * NP);
 }
 
-// reference gradients of two tiles at node k, as 2D independent chains, with
-// the rows of D read from shared memory at every use (sD + i_b NP for axis b):
-// holding them in registers across the streaming kernel's velocity loop made
-// it spill
+// reference gradients of two tiles at node k, as 2D independent chains, each
+// subtracted from a start value: oa[b] = init[b] - sum_m D[i_b][m] ta[...] and
+// ob[b] = init[b] - sum_m D[i_b][m] tb[...], every term an fma (the streaming
+// kernel starts both from t v_b).  The rows of D are read from shared memory at
+// every use (sD + i_b NP for axis b): holding them in registers across the
+// streaming kernel's velocity loop made it spill
 __device__ __forceinline__ double lds(const double* p) { return *(volatile const double*)p; }
 
 template <int D, int NP>
-__device__ __forceinline__ void grad_ref2(const double* sD, const NodeIdx<D, NP>& ix,
-                                            const double* __restrict__ ta,
-                                            const double* __restrict__ tb, int k, double (&oa)[D],
-                                            double (&ob)[D]) {
+__device__ __forceinline__ void grad_ref2_from(const double* sD, const NodeIdx<D, NP>& ix,
+                                               const double* __restrict__ ta,
+                                               const double* __restrict__ tb, int k,
+                                               const double (&init)[D], double (&oa)[D],
+                                               double (&ob)[D]) {
   constexpr int st[3] = {1, NP, NP * NP};
   int k0[D];
 #pragma unroll
   for (int b = 0; b < D; ++b) {
     k0[b] = k - ix.i[b] * st[b];
     const double d0 = lds(sD + ix.i[b] * NP);
-    oa[b] = d0 * ta[k0[b]];
-    ob[b] = d0 * tb[k0[b]];
+    oa[b] = fma(-d0, ta[k0[b]], init[b]);
+    ob[b] = fma(-d0, tb[k0[b]], init[b]);
   }
 #pragma unroll
   for (int m = 1; m < NP; ++m)
 #pragma unroll
     for (int b = 0; b < D; ++b) {
       const double dm = lds(sD + ix.i[b] * NP + m);
-      oa[b] = fma(dm, ta[k0[b] + m * st[b]], oa[b]);
-      ob[b] = fma(dm, tb[k0[b] + m * st[b]], ob[b]);
+      oa[b] = fma(-dm, ta[k0[b] + m * st[b]], oa[b]);
+      ob[b] = fma(-dm, tb[k0[b] + m * st[b]], ob[b]);
     }
 }
 
@@ -688,19 +691,41 @@ __device__ __forceinline__ void rhs_compute(const View& v, const double* sD, con
 #pragma unroll
       for (int b = 0; b < D; ++b) c[b] = L::template cdot<A>(J[b]);
     }
-    double dA[D], dB[D];
-    grad_ref2<D, NP>(sD, ix, sg + (A - 1) * NT + lb, sg + (B - 1) * NT + lb, k, dA, dB);
     // r_A = M_e (t e_A.v - e_A.grad g_A), r_B = -M_e (t e_A.v - e_A.grad g_B), e_B = -e_A
-    double cv = c[0] * vv[0];
+    double rA, rB;
+    if constexpr (L::TV_START) {
+      // = sum_b c_b (t v_b - d_b g_A) and -sum_b c_b (t v_b - d_b g_B): each
+      // derivative chain starts from t v_b, so every term of it is an fma
+      double tv[D];
 #pragma unroll
-    for (int b = 1; b < D; ++b) cv = fma(c[b], vv[b], cv);
-    const double tcv = T * cv;
-    double rA = fma(-c[0], dA[0], tcv);
-    double rB = fma(c[0], dB[0], -tcv);
+      for (int b = 0; b < D; ++b) tv[b] = T * vv[b];
+      double xA[D], xB[D];
+      grad_ref2_from<D, NP>(sD, ix, sg + (A - 1) * NT + lb, sg + (B - 1) * NT + lb, k, tv, xA,
+                            xB);
+      rA = c[0] * xA[0];
+      rB = -c[0] * xB[0];
 #pragma unroll
-    for (int b = 1; b < D; ++b) {
-      rA = fma(-c[b], dA[b], rA);
-      rB = fma(c[b], dB[b], rB);
+      for (int b = 1; b < D; ++b) {
+        rA = fma(c[b], xA[b], rA);
+        rB = fma(-c[b], xB[b], rB);
+      }
+    } else {
+      // t (c.v) once per pair, minus the derivatives nA = -grad g_A, nB = -grad g_B
+      const double zero[D] = {};
+      double nA[D], nB[D];
+      grad_ref2_from<D, NP>(sD, ix, sg + (A - 1) * NT + lb, sg + (B - 1) * NT + lb, k, zero, nA,
+                            nB);
+      double cv = c[0] * vv[0];
+#pragma unroll
+      for (int b = 1; b < D; ++b) cv = fma(c[b], vv[b], cv);
+      const double tcv = T * cv;
+      rA = fma(c[0], nA[0], tcv);
+      rB = fma(-c[0], nB[0], -tcv);
+#pragma unroll
+      for (int b = 1; b < D; ++b) {
+        rA = fma(c[b], nA[b], rA);
+        rB = fma(-c[b], nB[b], rB);
+      }
     }
     if (slot >= 0) {
       const double gA = sg[(A - 1) * NT + lb + k], gB = sg[(B - 1) * NT + lb + k];

@@ -14,6 +14,11 @@ metric array holds M_e S J^-1, so the mass and the speed scale cost nothing):
                                             cubic sets: (k-1) d adds; D3Q13: none
                                             (its d fma per pair are done once per
                                             mesh, k_pair_metric, and c is read)
+  then, for D2Q9 and D3Q13 (one t v per moving weight):
+  per node and moving weight, t v_b         d mul
+  per moving velocity                       d chains t v_b - d_b g (n fma
+                                            each), c.x: 1 mul + (d-1) fma
+  and for the cubic sets (two or three weights, t c.v formed per pair):
   per velocity pair, t c.v                  1 mul + (d-1) fma, 1 mul
   per moving velocity                       d derivatives, d fma (t c.v - c.dg)
   wall records, per moving velocity         1 sub + 1 fma
@@ -36,6 +41,10 @@ _DIM = {"D2Q9": 2, "D3Q13": 3, "D3Q19": 3, "D3Q27": 3}
 # sets whose pair coefficients M_e S J^-1 C are stored per node (k_rhs reads
 # (Q-1)/2 x d of them instead of the d x d metric)
 _STORED_PAIRS = ("D3Q13",)
+# sets whose streaming derivative chains start from t v (one product per moving
+# weight and node), and the number of distinct weights of the moving velocities
+_TV_START = ("D2Q9", "D3Q13")
+_MOVING_WEIGHTS = {"D2Q9": 2, "D3Q13": 1, "D3Q19": 2, "D3Q27": 3}
 
 
 def _pair_coeff_work(lattice, d):
@@ -57,11 +66,19 @@ def rhs_work_per_node(lattice, N):
     ops = d * dv["ops"] + 1 + d
     flops = d * dv["flops"] + 1 + 2 * d
     po, pf = _pair_coeff_work(lattice, d)
-    P = M // 2
-    ops += po + P * (d + 1)
-    flops += pf + P * (2 * d - 1 + 1)
-    per_v_ops = d * dv["ops"] + d
-    per_v_flops = d * dv["flops"] + 2 * d
+    ops += po
+    flops += pf
+    if lattice in _TV_START:
+        ops += _MOVING_WEIGHTS[lattice] * d
+        flops += _MOVING_WEIGHTS[lattice] * d
+        per_v_ops = d * n + d
+        per_v_flops = d * 2 * n + 2 * d - 1
+    else:
+        P = M // 2
+        ops += P * (d + 1)
+        flops += P * (2 * d - 1 + 1)
+        per_v_ops = d * dv["ops"] + d
+        per_v_flops = d * dv["flops"] + 2 * d
     return {"ops": ops + M * per_v_ops, "flops": flops + M * per_v_flops}
 
 

@@ -57,7 +57,11 @@ def test_flat_wall_angle_with_thinner_interface():
     """At delta / R = 0.2 (32x16 quads, N = 4, delta = 0.05) the drops of 90 and
     120 degrees, which at delta / R = 0.4 evaporate or settle low, hold their
     prescribed angle to within 1.5 degrees (device moments; force_split = 1; one
-    batch run to KE_max < 1e-14, as in bench.py --angle-study)."""
+    batch, each drop measured when its KE_max first falls below 1e-14, as in
+    bench.py --angle-study).  Started at the bulk densities, the 90-degree drop
+    gives the vapour 17 % of its area, comes to rest near 1.6e5 steps, and
+    rearranges later (KE_max back near 1e-7 around 2.2e5 steps while it sheds
+    another 0.6 % of its area), so it is measured at its first rest."""
     from paper_2609_00535_b300 import semlbm
     b = semlbm.Batch()
     runs = {}
@@ -67,18 +71,24 @@ def test_flat_wall_angle_with_thinner_interface():
         s = semlbm.Solver.from_case(c)
         s.set_density(c.rho0)
         runs[b.add(s)] = (deg, s)
-    for _ in range(100):
+    measured = {}
+    done = 0
+    while runs and done < 240000:
         b.step(2000)
+        done += 2000
         d = b.diagnostics()
-        if all(d[k]["ke_max"] < 1e-14 or d[k]["status"] != 0 for k in runs):
-            break
-    for slot, (deg, s) in runs.items():
-        assert d[slot]["status"] == 0 and d[slot]["ke_max"] < 1e-13, (deg, d[slot])
-        th = wetting.contact_angle(s.wetting_moments(0), 2, delta=0.05)
-        assert abs(th - deg) < 1.5, (deg, th)
+        for slot in list(runs):
+            deg, s = runs[slot]
+            assert d[slot]["status"] == 0, (deg, d[slot])
+            if d[slot]["ke_max"] < 1e-14:
+                measured[deg] = (done, wetting.contact_angle(s.wetting_moments(0), 2, delta=0.05))
+                b.remove(slot)
+                s.close()
+                del runs[slot]
+    assert not runs, ("not at rest within 2.4e5 steps", [deg for deg, _ in runs.values()])
+    for deg, (steps, th) in measured.items():
+        assert abs(th - deg) < 1.5, (deg, steps, th)
     b.close()
-    for _, s in runs.values():
-        s.close()
 
 
 @pytest.mark.parametrize("deg", [60, 120])
